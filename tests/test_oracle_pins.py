@@ -1,0 +1,371 @@
+"""Pins of the FP64 oracle to the paper's worked examples and to mathematics
+that does not depend on the oracle's own code (brute force, exact rationals,
+closed-form distributions).  CPU only."""
+import itertools
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2308_15020_gb300 import gen
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def golden(name):
+    out = {}
+    with open(os.path.join(GOLD, name)) as fh:
+        for line in fh:
+            line = line.split("#", 1)[0].strip()
+            if not line:
+                continue
+            k, v = (s.strip() for s in line.split("=", 1))
+            out[k] = [Fraction(t) for t in v.split()]
+    return out
+
+
+def fl(xs):
+    return np.array([float(t) for t in xs])
+
+
+# ---------------------------------------------------------------------------------------------
+# Worked examples
+# ---------------------------------------------------------------------------------------------
+
+
+def test_example1_walsh_coefficients():
+    g = golden("example1_walsh.txt")
+    L, K = int(g["L"][0]), int(g["K"][0])
+    a = O.walsh_by_size(O.ATLEAST, K, L)  # a[m] on e_m
+    want = fl(g["coef_e4_to_e0"])[::-1]  # -> e0..e4
+    assert np.array_equal(a, want)
+    # symmetry: every subset of the same size has the same coefficient (Thm. corner sum)
+    for mask in range(1 << L):
+        m = bin(mask).count("1")
+        assert O.walsh_subset(O.ATLEAST, K, L, mask) == want[m]
+
+
+@pytest.mark.parametrize("route", ["bruteforce", "corners", "esp", "paper", "dp", "default"])
+def test_example2_gradient_all_routes(route):
+    g = golden("example2_gradient.txt")
+    K = int(g["K"][0])
+    v, dy = O.fe(O.ATLEAST, K, fl(g["x"]), route)
+    assert np.allclose(dy, fl(g["grad"]), rtol=0, atol=1e-14)
+    assert abs(v - (-59 / 128)) < 1e-14
+
+
+def test_example3_ftilde_and_value():
+    g = golden("example3_forward.txt")
+    L, K = int(g["L"][0]), int(g["K"][0])
+    w = np.exp(-2j * np.pi / (L + 1))
+    scale = float(g["ftilde_scale"][0])
+    ft = O.paper_ftilde(O.ATLEAST, K, L)
+    for j in range(L + 1):
+        coefs = fl(g[f"ftilde{j}"])
+        want = scale * sum(c * w**p for p, c in enumerate(coefs))
+        assert abs(ft[j] - want) < 1e-14, (j, ft[j], want)
+    v, _ = O.fe(O.ATLEAST, K, fl(g["x"]), "paper")
+    assert abs(v - float(g["WE"][0])) < 1e-14
+
+
+def test_gradsat_probabilities():
+    g = golden("gradsat_example.txt")
+    v, _ = O.fe(O.ATLEAST, 2, fl(g["x"]), "dp")
+    # FE = P(false) * (+1) + P(true) * (-1)
+    assert v == float(g["P_false"][0] - g["P_true"][0])
+    assert g["P_true"][0] + g["P_false"][0] == 1
+
+
+def _poly2(coef, x1, x2):
+    c, a1, a2, a12 = (float(t) for t in coef)
+    return c + a1 * x1 + a2 * x2 + a12 * x1 * x2
+
+
+def test_saddle_example_objective():
+    g = golden("saddle_example.txt")
+    inst = gen.from_lists(2, [(gen.OR, 0, [1, -2]), (gen.XOR, 1, [-1, 2])])
+    rng = np.random.default_rng(0)
+    pts = rng.uniform(-1, 1, size=(8, 2))
+    f, _ = O.eval_grad(inst, pts)
+    assert np.allclose(f, [_poly2(g["F"], *p) for p in pts], atol=1e-15)
+    # the inner point where the gradient vanishes
+    f0, g0 = O.eval_grad(inst, fl(g["stationary"])[None])
+    assert np.allclose(g0, 0.0, atol=1e-15)
+    # reweighted objective
+    w = fl(g["weights_after"])
+    f1, _ = O.eval_grad(inst, pts, weights=w)
+    assert np.allclose(f1, [_poly2(g["F_after"], *p) for p in pts], atol=1e-15)
+
+
+def test_local_optimum_example_gradient():
+    g = golden("local_example.txt")
+    inst = gen.from_lists(4, [(gen.XOR, 1, [1, 2]), (gen.XOR, 1, [2, 3]), (gen.XOR, 1, [3, 4])])
+    p = fl(g["point"])[None]
+    f, _ = O.eval_grad(inst, p)
+    assert f[0] == 1 * -1 + -1 * -1 + -1 * 1  # F = x1x2 + x2x3 + x3x4
+    _, gr = O.eval_grad(inst, p, weights=fl(g["weights_after"]))
+    assert np.allclose(gr[0], fl(g["grad_after"]), atol=1e-15)
+
+
+# ---------------------------------------------------------------------------------------------
+# Definitions on tiny inputs: corners, brute force, ESPs
+# ---------------------------------------------------------------------------------------------
+
+CASES = [(O.OR, 0), (O.XOR, 0), (O.XOR, 1)] + [(O.ATLEAST, k) for k in range(0, 7)]
+
+
+@pytest.mark.parametrize("ctype,param", CASES)
+@pytest.mark.parametrize("L", [1, 2, 3, 5, 6])
+def test_corners_equal_truth(ctype, param, L):
+    """At every cube corner FE is -1 iff the constraint holds (Thm. "Walsh Transform")."""
+    for bits in itertools.product([-1.0, 1.0], repeat=L):
+        y = np.array(bits)
+        ntrue = int((y < 0).sum())
+        if ctype == O.OR:
+            truth = ntrue >= 1
+        elif ctype == O.XOR:
+            truth = (ntrue % 2) == param
+        else:
+            truth = ntrue >= param
+        for route in ("default", "dp", "bruteforce"):
+            v, _ = O.fe(ctype, param, y, route)
+            assert v == (-1.0 if truth else 1.0), (route, bits, v)
+
+
+@pytest.mark.parametrize("ctype,param", CASES)
+@pytest.mark.parametrize("L", [1, 4, 7, 9])
+def test_routes_agree_small(ctype, param, L):
+    rng = np.random.default_rng(L * 31 + ctype * 7 + param)
+    for _ in range(4):
+        y = rng.uniform(-1, 1, L)
+        ref, dref = O.fe(ctype, param, y, "bruteforce")
+        for route in ("corners", "esp", "paper", "dp", "default"):
+            v, d = O.fe(ctype, param, y, route)
+            assert abs(v - ref) < 1e-12, route
+            assert np.allclose(d, dref, atol=1e-12), route
+
+
+def test_esp_matches_subset_sums():
+    rng = np.random.default_rng(5)
+    for L in range(0, 9):
+        y = rng.uniform(-1, 1, L)
+        e = O.esp(y)
+        for m in range(L + 1):
+            want = sum(math.prod(y[list(S)]) for S in itertools.combinations(range(L), m))
+            assert abs(e[m] - want) < 1e-13
+
+
+def test_walsh_by_size_matches_theorem_sum():
+    for L in range(1, 11):
+        for ctype, param in [(O.OR, 0), (O.XOR, 1), (O.ATLEAST, (L + 1) // 2)]:
+            a = O.walsh_by_size(ctype, param, L)
+            for m in range(L + 1):
+                mask = (1 << m) - 1
+                assert a[m] == O.walsh_subset(ctype, param, L, mask)
+
+
+# ---------------------------------------------------------------------------------------------
+# Long constraints: exact rationals, closed-form distributions, finite differences
+# ---------------------------------------------------------------------------------------------
+
+
+def _exact_fe_esp(ctype, param, y_fr):
+    """FE = sum_m a_m e_m (Eq. effi_eval) in exact rationals, a_m from the
+    Krawtchouk grouping of the theorem's corner sum with exact integers."""
+    L = len(y_fr)
+    val = [O.value(ctype, param, L, s) for s in range(L + 1)]
+    e = [Fraction(0)] * (L + 1)
+    e[0] = Fraction(1)
+    for yi in y_fr:
+        for m in range(L, 0, -1):
+            e[m] += yi * e[m - 1]
+    fe = Fraction(0)
+    for m in range(L + 1):
+        tot = 0
+        for s in range(L + 1):
+            kr = sum((-1) ** t * math.comb(m, t) * math.comb(L - m, s - t) for t in range(0, min(m, s) + 1))
+            tot += val[s] * kr
+        fe += Fraction(tot, 2**L) * e[m]
+    return fe
+
+
+@pytest.mark.parametrize("L", [16, 40, 64])
+def test_dp_matches_exact_rationals(L):
+    rng = np.random.default_rng(L)
+    k = rng.integers(-64, 65, size=L)
+    y = k / 64.0
+    y_fr = [Fraction(int(t), 64) for t in k]
+    for ctype, param in [(O.ATLEAST, L // 2), (O.ATLEAST, L // 2 + L // 8), (O.OR, 0), (O.XOR, 1)]:
+        exact = _exact_fe_esp(ctype, param, y_fr)
+        v, _ = O.fe(ctype, param, y, "dp")
+        assert abs(Fraction(v) - exact) < Fraction(1, 10**13), (ctype, param)
+
+
+def _binom_tail(L, K, p_fr):
+    q = 1 - p_fr
+    return sum(math.comb(L, s) * p_fr**s * q ** (L - s) for s in range(K, L + 1))
+
+
+@pytest.mark.parametrize("L,K", [(64, 32), (257, 140), (512, 256), (512, 300), (512, 200)])
+@pytest.mark.parametrize("ynum", [0, 16, -40])
+def test_dp_binomial_closed_form(L, K, ynum):
+    """All literals equal: S ~ Binomial(L, p) with p = (1 - y)/2."""
+    y_fr = Fraction(ynum, 64)
+    p = (1 - y_fr) / 2
+    fe_exact = 1 - 2 * _binom_tail(L, K, p)
+    # dFE/dy_i = P(Binomial(L-1, p) = K-1)
+    d_exact = math.comb(L - 1, K - 1) * p ** (K - 1) * (1 - p) ** (L - K)
+    y = np.full(L, float(y_fr))
+    v, d = O.fe(O.ATLEAST, K, y, "dp")
+    assert abs(v - float(fe_exact)) < 1e-13
+    assert np.allclose(d, float(d_exact), rtol=1e-11, atol=1e-300)
+
+
+@pytest.mark.parametrize("L", [3, 50, 300, 512])
+def test_dp_generic_equals_closed_forms(L):
+    """The DP with the OR / XOR truth tables reproduces the closed forms."""
+    rng = np.random.default_rng(L)
+    y = rng.uniform(-1, 1, L)
+    for ctype, param, cf in [(O.OR, 0, O.fe_or), (O.XOR, 1, lambda yy: O.fe_xor(1, yy)), (O.XOR, 0, lambda yy: O.fe_xor(0, yy))]:
+        v1, d1 = O.fe(ctype, param, y, "dp")
+        v2, d2 = cf(y)
+        assert abs(v1 - v2) < 1e-13
+        assert np.allclose(d1, d2, atol=1e-13)
+    # at-least-1 is the clause
+    v1, d1 = O.fe(O.ATLEAST, 1, y, "dp")
+    v2, d2 = O.fe_or(y)
+    assert abs(v1 - v2) < 1e-13 and np.allclose(d1, d2, atol=1e-13)
+
+
+@pytest.mark.parametrize("L,K", [(8, 4), (64, 30), (200, 100), (512, 260)])
+def test_gradient_is_exact_central_difference(L, K):
+    """FE is multilinear, so (FE(y_i=+1) - FE(y_i=-1))/2 equals dFE/dy_i exactly."""
+    rng = np.random.default_rng(L + K)
+    y = rng.uniform(-1, 1, L)
+    _, d = O.fe(O.ATLEAST, K, y, "dp")
+    for i in rng.choice(L, size=min(L, 12), replace=False):
+        yp, ym = y.copy(), y.copy()
+        yp[i], ym[i] = 1.0, -1.0
+        fd = (O.fe(O.ATLEAST, K, yp, "dp")[0] - O.fe(O.ATLEAST, K, ym, "dp")[0]) / 2
+        assert abs(fd - d[i]) < 1e-13
+        assert d[i] >= -1e-15  # dFE/dy_i = P_{-i}(S = K-1) >= 0 for at-least-K
+
+
+@pytest.mark.parametrize("L", [40, 128, 512])
+def test_value_in_range_and_monotone(L):
+    rng = np.random.default_rng(L)
+    for _ in range(5):
+        y = rng.uniform(-1, 1, L)
+        K = int(rng.integers(1, L + 1))
+        v, d = O.fe(O.ATLEAST, K, y, "dp")
+        assert -1.0 - 1e-15 <= v <= 1.0 + 1e-15
+        assert (d >= -1e-15).all()
+        vo, do = O.fe_or(y)
+        assert -1 <= vo <= 1 and (do >= 0).all()
+
+
+def test_degenerate_cardinality():
+    y = np.random.default_rng(0).uniform(-1, 1, 20)
+    v, d = O.fe(O.ATLEAST, 0, y, "dp")  # always satisfied
+    assert v == -1.0 and np.all(d == 0)
+    v, d = O.fe(O.ATLEAST, 21, y, "dp")  # never satisfied
+    assert v == 1.0 and np.all(d == 0)
+
+
+def test_paper_form_loses_precision_with_length():
+    """The paper's literal form cancels for long constraints (Conclusion's precision remark)."""
+    rng = np.random.default_rng(1)
+    errs = {}
+    for L in (8, 24, 48):
+        y = rng.uniform(-1, 1, L)
+        ref, _ = O.fe(O.ATLEAST, L // 2, y, "dp")
+        v, _ = O.fe(O.ATLEAST, L // 2, y, "paper")
+        errs[L] = abs(v - ref)
+    assert errs[8] < 1e-13
+    assert errs[48] > errs[8]
+
+
+# ---------------------------------------------------------------------------------------------
+# Instance level: certificate, checker twin, restart draws, one CLS round
+# ---------------------------------------------------------------------------------------------
+
+
+def _truth(ctype, param, lits, assign):
+    vals = [(assign[abs(l) - 1] * (1 if l > 0 else -1)) < 0 for l in lits]
+    if ctype == O.OR:
+        return any(vals)
+    if ctype == O.XOR:
+        acc = False
+        for t in vals:
+            acc ^= t
+        return acc == bool(param & 1)
+    return sum(vals) >= param
+
+
+def test_checker_twin_and_certificate():
+    inst = gen.concat([gen.random_ksat(30, 100, 3, 1), gen.random_xor(30, 10, 2, 6, 1, signs=True),
+                       gen.random_atleast(30, 5, 4, 12, 1)])
+    x = gen.corner_points(64, 30, 3, dtype=np.float64)
+    sat, nun = O.check(inst, x)
+    f, _ = O.eval_grad(inst, x)
+    for b in range(x.shape[0]):
+        z = np.where(x[b] < 0, -1.0, 1.0)
+        want = sum(not _truth(*inst.constraint(c), z) for c in range(inst.m))
+        assert nun[b] == want and sat[b] == (want == 0)
+        # at corners F(sgn x) = #violated - #satisfied (Thm. "SAT Certificate")
+        fz, _ = O.eval_grad(inst, z[None])
+        assert fz[0] == 2 * want - inst.m
+    # F >= -sum w everywhere in the cube
+    xs = gen.uniform_points(32, 30, 4, dtype=np.float64)
+    fs, _ = O.eval_grad(inst, xs)
+    assert (fs >= -inst.m - 1e-9).all()
+
+
+def test_planted_instances_are_satisfied():
+    for make in (gen.uniform_3sat_100, gen.cnf_xor_2000):
+        inst = make(3, planted=True)
+        sat, nun = O.check(inst, inst.planted[None].astype(np.float64))
+        assert sat[0] == 1 and nun[0] == 0
+        f, _ = O.eval_grad(inst, inst.planted[None].astype(np.float64))
+        assert f[0] == -inst.weights.sum()
+
+
+def test_signed_zero_is_false():
+    inst = gen.from_lists(1, [(gen.OR, 0, [1])])
+    sat, _ = O.check(inst, np.array([[0.0], [-0.0], [-1e-300], [1.0]]))
+    assert list(sat) == [0, 0, 1, 0]
+    with pytest.raises(ValueError):
+        O.check(inst, np.array([[np.nan]]))
+
+
+def test_splitmix64_published_first_output():
+    # splitmix64 started at state 0 returns 0xE220A8397B1DCDAF first (Steele et al. 2014 / Vigna)
+    assert O.splitmix64(0) == 0xE220A8397B1DCDAF
+
+
+def test_uniform_draws():
+    vals = np.array([O.uniform(7, 2, b, v) for b in range(20) for v in range(500)])
+    assert vals.min() >= -1.0 and vals.max() < 1.0
+    assert np.all(vals * 2**23 == np.round(vals * 2**23))
+    assert abs(vals.mean()) < 0.02 and abs(vals.var() - 1 / 3) < 0.02
+    assert O.uniform(7, 2, 3, 4) != O.uniform(7, 3, 3, 4)
+
+
+def test_step_is_pgd_then_check_then_restart():
+    inst = gen.uniform_3sat_100(0)
+    x0 = gen.uniform_points(6, inst.n, 1, dtype=np.float64)
+    f, g = O.eval_grad(inst, x0)
+    x1, solved, nun = O.step(inst, x0, T=1, lr=0.1, seed=5, epoch=0, restart=False)
+    assert np.array_equal(x1, np.clip(x0 - 0.1 * g, -1, 1))
+    s2, n2 = O.check(inst, x1)
+    assert np.array_equal(s2, solved) and np.array_equal(n2, nun)
+    x2, solved2, _ = O.step(inst, x0, T=1, lr=0.1, seed=5, epoch=3, b_offset=10, restart=True)
+    for b in range(6):
+        if not solved2[b]:
+            want = [O.uniform(5, 3, 10 + b, v) for v in range(inst.n)]
+            assert np.array_equal(x2[b], want)
+        else:
+            assert np.array_equal(x2[b], x1[b])
