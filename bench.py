@@ -1,0 +1,403 @@
+#!/usr/bin/env python
+"""Benchmark of the FastFourierSAT hot path on one node.
+
+One benchmark step is one ``ffsat_step`` call: T projected-gradient iterations
+(each a full evaluation of F and grad F over all B restart points and the
+projected update), then the exact sign check and the uniform restart of every
+point that is not a model -- one pass of the whole hot path, one kernel launch.
+
+Metric: literal-gradients per second = B * sum_c |c| * T / step time.
+Default workload: hybrid CNF-XOR, n = 2000, 8400 random 3-clauses + 200 XOR of
+length U{10..40}, B = 256 restart points, FP32 (stable node form), T = 200,
+lr = 0.1.  Inputs are seeded synthetic stand-ins for the paper's benchmark
+families; the L2 cache is flushed (256 MiB write) before every timed step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                       [--workload cnf_xor_n2000|cnf_card_n20000|3sat_n100] [--T T]
+For N > 1 launch under torch.distributed.run: every rank runs its own B points
+(weak scaling; points are independent, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2308_15020_gb300 import gen  # noqa: E402
+
+METRIC = "literal-grads/s (B·Σ|c| per s) FP32-scaled vs FP64 at 1e-4 rel; time-to-SAT"
+UNIT = "literal-grads/s"
+
+# workload name -> (instance builder, B, dtype, T, lr)
+WORKLOADS = {
+    "cnf_xor_n2000": (gen.cnf_xor_2000, 256, "f32", 200, 0.1),
+    "cnf_card_n20000": (gen.cnf_card_20000, 1024, "f32", 4, 0.1),
+    "3sat_n100": (gen.uniform_3sat_100, 32, "f64", 200, 0.1),
+}
+
+FP32_LANES_PER_SM = 128
+# algorithmic FP32 flops of the node path per (node, literal): factor (2 FMA = 4),
+# suffix product (complex multiply, 6), prefix product (6), Re(pre * suf) (3)
+NODE_FLOPS = 19
+# closed forms per literal: factor (FMA, 2), all-but-one product (2 multiplies) and weight (1)
+CLOSED_FLOPS = 5
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2308_15020_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def profile_traffic(kernel: str, workload: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if it matches the current kernel source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch_full"])
+    except (KeyError, ValueError):
+        return None
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def instance_stats(inst):
+    L = inst.lengths()
+    ty = inst.ctype
+    return {"n": int(inst.n), "m": int(inst.m), "nnz": int(inst.nnz), "L": L, "type": ty, "param": inst.param}
+
+
+def algorithmic_work(st, B: int, T: int):
+    """FP32 flops and minimal DRAM bytes of one step launch."""
+    L = st["L"]
+    node = (st["type"] == 2) & (st["param"] > 0) & (st["param"] <= L)
+    J = (L[node] + 1) // 2 + 1
+    flops_pt = float(np.sum(J.astype(np.float64) * L[node] * NODE_FLOPS)) + float(np.sum(L[~node])) * CLOSED_FLOPS
+    flops = flops_pt * B * T
+    bytes_ = 2.0 * B * st["n"] * 4 + st["nnz"] * 4.0 + st["m"] * 16.0 + B * 5.0
+    return flops, bytes_, bool(node.any() and np.sum(J * L[node]) > np.sum(L[~node]))
+
+
+# ---------------------------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: str):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def visible_device_index(local_rank: int) -> str:
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if cvd:
+        ids = [s.strip() for s in cvd.split(",") if s.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+# ---------------------------------------------------------------------------------------------
+# CPU oracle legs
+# ---------------------------------------------------------------------------------------------
+
+def oracle_rate(inst, x_sample, T: int, lr: float):
+    """literal-grads/s of the FP64 oracle's projected-GD round on a sample (all host threads)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    t0 = time.perf_counter()
+    O.step(inst, x_sample, T=T, lr=lr, seed=0, restart=True)
+    dt = time.perf_counter() - t0
+    return x_sample.shape[0] * inst.nnz * T / dt, dt, O.max_threads()
+
+
+def calibrate_sample(inst, n_total_pts: int, T: int, lr: float, target_s: float):
+    """Choose (points, iterations) of the workload so the oracle runs about target_s seconds."""
+    x1 = gen.uniform_points(1, inst.n, 99, dtype=np.float64)
+    _, dt, _ = oracle_rate(inst, x1, 1, lr)
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    threads = O.max_threads()
+    per_pt_iter = max(dt, 1e-6)
+    budget = target_s * threads / per_pt_iter  # point-iterations
+    T_s = int(max(1, min(T, budget // max(1, min(n_total_pts, threads)))))
+    B_s = int(max(1, min(n_total_pts, budget // T_s)))
+    B_s = max(1, (B_s // threads) * threads) if B_s >= threads else B_s
+    return B_s, T_s
+
+
+def cpu_baseline(inst, B: int, T: int, lr: float, target_s: float = 12.0):
+    B_s, T_s = calibrate_sample(inst, B, T, lr, target_s)
+    xs = gen.uniform_points(B_s, inst.n, 0, dtype=np.float64)
+    rate, dt, threads = oracle_rate(inst, xs, T_s, lr)
+    return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{B_s} of {B} points x {T_s} of {T} PGD iterations, FP64 oracle, {dt:.1f} s"}
+
+
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    build, B, dt_name, T, lr = WORKLOADS[args.workload]
+    T = args.T or T
+    inst = build(0)
+    B_s, T_s = calibrate_sample(inst, B, T, lr, target_s=args.ref_seconds)
+    xs = gen.uniform_points(B_s, inst.n, 0, dtype=np.float64)
+    for _ in range(args.warmup):
+        oracle_rate(inst, xs, max(1, T_s // 4), lr)
+    times = []
+    for _ in range(args.steps):
+        _, dt, threads = oracle_rate(inst, xs, T_s, lr)
+        times.append(dt)
+    tot = sum(times)
+    value = B_s * inst.nnz * T_s * len(times) / tot
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded generator)",
+        "config": {"workload": args.workload, "B": B, "n": inst.n, "m": inst.m, "nnz": inst.nnz,
+                   "pgd_iters_per_step": T, "lr": lr, "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{B_s} of {B} points x {T_s} of {T} PGD iterations per step, FP64 oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU leg
+# ---------------------------------------------------------------------------------------------
+
+def run_ours(args, rank: int, world: int, local_rank: int):
+    import torch
+
+    from paper_2308_15020_gb300 import ffsat
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist  # noqa: F811
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    build, B, dtname, T, lr = WORKLOADS[args.workload]
+    T = args.T or T
+    B = args.B or B
+    inst = build(0)
+    st = instance_stats(inst)
+    h = ffsat.Instance(inst)
+    tdt = torch.float32 if dtname == "f32" else torch.float64
+    # this rank's points: global indices [rank*B, (rank+1)*B)
+    x_host_np = gen.uniform_points(B, inst.n, 1000 + rank)
+    x_host = torch.from_numpy(x_host_np).to(tdt).pin_memory()
+    x0 = x_host.cuda()
+    x = x0.clone()
+    solved = torch.empty(B, dtype=torch.uint8, device="cuda")
+    nun = torch.empty(B, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    epoch = [0]
+
+    def one_step():
+        h.step(x, T=T, lr=lr, seed=7, epoch=epoch[0], b_offset=rank * B, restart=True, solved=solved, n_unsat=nun,
+               stream=stream)
+        epoch[0] += 1
+
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize()
+    h.sync_status()
+    launches_per_step = ffsat.last_launch_count()
+
+    # ---- device-timed region ----
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(visible_device_index(local_rank)) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    for s, e in evs:
+        flush.zero_()
+        s.record(stream)
+        one_step()
+        e.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    h.sync_status()
+    per = [s.elapsed_time(e) for s, e in evs]
+    total_ms = sum(per)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    work = B * inst.nnz * T
+    value = world * work * args.steps / (total_ms / 1e3)
+
+    # ---- end-to-end through host buffers ----
+    solved_h = torch.empty(B, dtype=torch.uint8).pin_memory()
+    nun_h = torch.empty(B, dtype=torch.int32).pin_memory()
+    e2e_ms = []
+    for i in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        x.copy_(x_host, non_blocking=True)
+        one_step()
+        solved_h.copy_(solved, non_blocking=True)
+        nun_h.copy_(nun, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = sum(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * work * args.steps / (e2e_total / 1e3)
+    h2d = B * inst.n * x_host.element_size()
+    d2h = B * (solved_h.element_size() + nun_h.element_size())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the fused step kernel (the only kernel of a step) ----
+    peaks, peak_src = load_peaks()
+    flops, bytes_, alu_bound = algorithmic_work(st, B, T)
+    launch_s = (total_ms / args.steps) / 1e3 / max(1, launches_per_step)
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    if alu_bound:
+        peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        achieved = flops / launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "peak_source": f"FP32 FMA lanes x 2 x {sm_max:.0f} MHz (max SM clock, {peak_src} peaks file)",
+                "algorithmic_per_launch": flops}
+    else:
+        peak = float(peaks["hbm_gbs"])
+        achieved = bytes_ / launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_per_launch": bytes_}
+    roof["traffic"] = profile_traffic("ffsat_fused", args.workload)
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(inst, B, T, lr, target_s=args.cpu_seconds)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": dtname, "data": "synthetic (seeded generator)",
+        "config": {"workload": args.workload, "B": B, "n": inst.n, "m": inst.m, "nnz": inst.nnz,
+                   "pgd_iters_per_step": T, "lr": lr, "form": "stable",
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world} (points sharded, no collective)"},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk,
+        "kernel_source_hash": kernel_source_hash(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cnf_xor_n2000", choices=list(WORKLOADS))
+    ap.add_argument("--T", type=int, default=0, help="PGD iterations per step (0 = workload default)")
+    ap.add_argument("--B", type=int, default=0, help="restart points per GPU (0 = workload default)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-seconds", type=float, default=4.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,191 @@
+/*
+ * ffsat.h — C ABI of the GB300 FastFourierSAT hot path (libffsat.so).
+ *
+ * The library evaluates the relaxed objective of a hybrid Boolean formula,
+ * F(x) = sum_c w_c FE_c(x) (Def. "Objective", Eq. objective), and its gradient
+ * at B restart points x in [-1,1]^n at once, runs fixed-step projected
+ * gradient descent with restarts (Alg. 1 with App. A.3 "Projected Gradient
+ * Descent"), and checks assignments exactly (Thm. "SAT Certificate").
+ *
+ * Conventions.
+ *  - -1 encodes True and +1 False (Preliminaries, "Walsh Expansions").
+ *  - Literals are DIMACS-style signed 1-based integers: +v is x_v, -v is -x_v.
+ *  - Constraint types: FFSAT_OR (clause), FFSAT_XOR (satisfied iff the number of
+ *    True literals has parity `param`; param=1 is the usual exclusive-or),
+ *    FFSAT_ATLEAST (satisfied iff at least `param` literals are True).
+ *  - FE_c is the Walsh expansion of c (Thm. "Walsh Transform"): -1 at satisfying
+ *    corners, +1 at violating corners, multilinear in between.
+ *  - Points are row-major [B, n] arrays in device memory, float32 or float64.
+ *  - Every entry point returns FFSAT_OK (0) or a negative error code;
+ *    ffsat_last_error() returns a thread-local message for the last failure.
+ *  - Work is enqueued asynchronously on the given CUDA stream (a cudaStream_t
+ *    passed as void*; NULL = legacy default stream).  Argument errors are
+ *    returned synchronously; device-side errors (NaN inputs) are latched in a
+ *    device status word and reported by ffsat_sync_status().
+ *  - The caller owns every x / f / g / sat / solved buffer; the library never
+ *    frees them.  The library owns the instance and its device tables.
+ *  - An instance is read-only during ffsat_eval_grad / ffsat_check, which may run
+ *    concurrently on different streams.  ffsat_step uses per-instance scratch for
+ *    large n and ffsat_set_weights rewrites device tables: do not overlap those
+ *    with other calls on the same instance.
+ */
+#ifndef FFSAT_H
+#define FFSAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ffsat_instance ffsat_instance;
+
+enum { FFSAT_OR = 0, FFSAT_XOR = 1, FFSAT_ATLEAST = 2 };
+enum { FFSAT_F32 = 0, FFSAT_F64 = 1 };
+/* Node parametrisation of the DFT evaluation (see ffsat_options.form). */
+enum { FFSAT_FORM_STABLE = 0, FFSAT_FORM_PAPER = 1 };
+
+#define FFSAT_OK 0
+#define FFSAT_ERR_ARG (-1)       /* NULL pointer, negative size, bad dtype/option */
+#define FFSAT_ERR_VAR_RANGE (-2) /* literal 0 or |literal| > n_vars */
+#define FFSAT_ERR_DUPVAR (-3)    /* a variable occurs twice in one constraint */
+#define FFSAT_ERR_EMPTY (-4)     /* constraint with no literals */
+#define FFSAT_ERR_PARAM (-5)     /* unknown type, parity not 0/1, K < 0, bad CSR */
+#define FFSAT_ERR_WEIGHT (-6)    /* negative or non-finite weight */
+#define FFSAT_ERR_TOOLONG (-7)   /* constraint longer than the kernels support */
+#define FFSAT_ERR_CUDA (-8)      /* a CUDA runtime call failed (message has the detail) */
+#define FFSAT_ERR_NAN (-9)       /* a NaN was found in x (latched on the device) */
+#define FFSAT_ERR_DEVICE (-10)   /* another device-side error was latched */
+
+/* Longest constraint accepted (literals). */
+#define FFSAT_MAX_LEN 512
+
+typedef struct ffsat_options {
+    /* FFSAT_FORM_STABLE (default): node factors q_i + p_i w^j with
+     * q_i = (1+y_i)/2, p_i = (1-y_i)/2 — the paper's polynomial prod_i(1 + y_i z)
+     * evaluated at z_j = (1-w^j)/(1+w^j) and scaled by ((1+w^j)/2)^L per node, so
+     * that every factor and every partial product has modulus <= 1 in FP32.
+     * FFSAT_FORM_PAPER: the paper's literal factors 1 + y_i w^j with weights
+     * b_j from the Walsh coefficients (Eq. forward / Eq. inverse); only for
+     * constraints of <= 60 literals (it cancels catastrophically above that). */
+    int32_t form;
+    /* 1: evaluate OR and XOR constraints through the node (DFT) kernel as well
+     * instead of their closed forms (cross-check / study mode). */
+    int32_t node_all;
+    /* Literals per lane in the node kernel: 0 = automatic (autotuned when
+     * `autotune` is set), else 8 or 16. */
+    int32_t node_r;
+    /* 1: time the candidate kernel variants on the device at load and keep the
+     * fastest (costs a few milliseconds per load). */
+    int32_t autotune;
+    /* CUDA device ordinal, -1 = the current device. */
+    int32_t device;
+} ffsat_options;
+
+typedef struct ffsat_step_args {
+    int32_t T;         /* projected-GD iterations per call (>= 0) */
+    int32_t restart;   /* 1: points whose sign vector is not a model restart uniformly */
+    double lr;         /* step size eta of x <- clip(x - eta * grad F(x), -1, 1) */
+    uint64_t seed;     /* restart seed */
+    uint64_t epoch;    /* outer-round counter (part of the restart draw's key) */
+    uint64_t b_offset; /* global index of point 0, so that sharded runs draw alike */
+} ffsat_step_args;
+
+typedef struct ffsat_info {
+    int32_t n, m;
+    int64_t nnz;
+    int32_t n_clause3;     /* clauses of <= 3 literals (thread-per-clause path) */
+    int32_t n_product;     /* OR/XOR constraints on the product (closed-form) path */
+    int32_t n_node;        /* constraints on the node (DFT) path */
+    int32_t n_const;       /* constraints whose value is constant (K <= 0 or K > L) */
+    int32_t n_tables;      /* distinct node tables */
+    int32_t n_tasks;       /* warp tasks per point and iteration */
+    int32_t node_r;        /* literals per lane chosen for the node kernel */
+    int32_t smem_mode_f32; /* 0: x and g in shared memory, 1: x only, 2: neither,
+                              3: x, g and the constraint data in shared memory */
+    int32_t smem_mode_f64;
+    int32_t threads_f32;   /* threads per CTA of the fused kernel */
+    int64_t node_lane_work; /* sum over node constraints of nodes x (lanes x R) per point */
+    int64_t device_bytes;  /* device memory held by the instance */
+} ffsat_info;
+
+/* Fill `opt` with the defaults (stable form, closed forms for OR/XOR,
+ * automatic node_r, autotune off, current device). */
+void ffsat_default_options(ffsat_options *opt);
+
+/* Build an instance from a CSR constraint list (all arrays in HOST memory):
+ *   row_ptr[n_cons+1] int64, row_ptr[0] = 0, non-decreasing;
+ *   lits[row_ptr[n_cons]] signed 1-based literals;
+ *   type[n_cons] FFSAT_OR / FFSAT_XOR / FFSAT_ATLEAST;
+ *   param[n_cons] parity (XOR, 0 or 1), K (ATLEAST, K >= 0; K > L is allowed and
+ *     makes the constraint constantly violated), ignored for OR;
+ *   weights[n_cons] finite, >= 0, or NULL for all ones.
+ * Validates everything before touching the device (errors above), then
+ * precomputes in FP64 on the host the DFT node tables of every distinct
+ * (type, length, parameter) — the conjugated coefficients of Eq. inverse,
+ * "computed in preprocessing" — buckets constraints by length and uploads all
+ * tables once.  `opt` may be NULL.  On success *out owns device memory until
+ * ffsat_free(). */
+int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, const int32_t *lits,
+                        const uint8_t *type, const int32_t *param, const double *weights,
+                        const ffsat_options *opt, ffsat_instance **out);
+
+/* Replace all constraint weights (HOST array of n_cons finite, non-negative values).
+ * Synchronous with respect to the host; callers must not run other work on the
+ * instance concurrently. */
+int ffsat_set_weights(ffsat_instance *inst, const double *weights);
+
+/* f[b] = F(x_b) (FP64, accumulated in FP64 across threads) and, if g != NULL,
+ * g[b,:] = grad F(x_b) for the B points of x (Def. "Objective"; gradient by the
+ * chain rule of Prop. "Chain rule", realised with prefix/suffix products).
+ *   x: device [B, n] of dtype (FFSAT_F32 or FFSAT_F64), read only;
+ *   f: device [B] double, or NULL;  g: device [B, n] of dtype, or NULL.
+ * B = 0 is a no-op. */
+int ffsat_eval_grad(ffsat_instance *inst, int32_t B, const void *x, int32_t dtype, double *f, void *g,
+                    void *stream);
+
+/* The plain FP64 comparator: the same mathematics in double precision with a
+ * naive mapping (one thread per (constraint, point), global atomics, no
+ * bucketing or shared-memory staging).  x, f, g: device double arrays
+ * ([B,n], [B], [B,n]); f and g are overwritten. */
+int ffsat_eval_grad_plain64(ffsat_instance *inst, int32_t B, const double *x, double *f, double *g,
+                            void *stream);
+
+/* One outer round of Alg. 1 for B points in place: args->T iterations of
+ * x <- clip(x - lr grad F(x), -1, 1) (App. A.3 with a fixed step), then the exact
+ * check of sgn(x) (sgn(x) = -1 iff x < 0), then, if args->restart, a uniform
+ * redraw of every point that is not a model.  All iterations run inside one
+ * kernel launch per call.
+ *   x: device [B, n] of dtype, updated in place;
+ *   solved: device [B] uint8 (1 iff sgn(x) satisfies every constraint), or NULL;
+ *   n_unsat: device [B] int32 (violated constraints at sgn(x) before any restart), or NULL. */
+int ffsat_step(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, const ffsat_step_args *args,
+               uint8_t *solved, int32_t *n_unsat, void *stream);
+
+/* Exact checker (Alg. 1, line 5, evaluated on integers rather than through F):
+ * sat[b] = 1 iff sgn(x_b) satisfies every constraint, regardless of weights;
+ * n_unsat[b] = number of violated constraints.  Either output may be NULL. */
+int ffsat_check(ffsat_instance *inst, int32_t B, const void *x, int32_t dtype, uint8_t *sat, int32_t *n_unsat,
+                void *stream);
+
+/* Synchronise `stream`, read and clear the instance's device status word:
+ * FFSAT_OK, FFSAT_ERR_NAN or FFSAT_ERR_DEVICE. */
+int ffsat_sync_status(ffsat_instance *inst, void *stream);
+
+/* Describe the instance's layout (host struct). */
+int ffsat_instance_info(const ffsat_instance *inst, ffsat_info *info);
+
+/* Number of kernel launches the last eval/step/check call on this thread enqueued. */
+int32_t ffsat_last_launch_count(void);
+
+/* Message for the last error on this thread ("" if none). */
+const char *ffsat_last_error(void);
+
+/* Release the instance and its device memory (NULL is ignored).  The caller must
+ * make sure no enqueued work still uses it. */
+void ffsat_free(ffsat_instance *inst);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FFSAT_H */

@@ -443,6 +443,57 @@ int orc_eval_grad(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *l
     return status;
 }
 
+int orc_eval_scale(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *lits,
+                   const uint8_t *type, const int32_t *param, const double *w,
+                   int32_t B, const double *x, double *sf, double *A, double floor, int floor_types,
+                   int nthreads) {
+    int nt = resolve_threads(nthreads);
+    int L = max_len(m, row_ptr);
+    int status = 0;
+#pragma omp parallel num_threads(nt)
+    {
+        double *y = (double *)malloc(sizeof(double) * (size_t)(L + 1));
+        double *dy = (double *)malloc(sizeof(double) * (size_t)(L + 1));
+#pragma omp for schedule(dynamic, 1)
+        for (int32_t b = 0; b < B; ++b) {
+            const double *xb = x + (size_t)b * n;
+            double *Ab = A + (size_t)b * n;
+            for (int32_t v = 0; v < n; ++v) Ab[v] = 0.0;
+            double acc = 0.0;
+            for (int32_t c = 0; c < m; ++c) {
+                int64_t a = row_ptr[c];
+                int Lc = (int)(row_ptr[c + 1] - a);
+                int bad = 0;
+                for (int i = 0; i < Lc; ++i) {
+                    int32_t lit = lits[a + i];
+                    int32_t v = (lit > 0 ? lit : -lit) - 1;
+                    if (v < 0 || v >= n) bad = 1;
+                    else y[i] = lit > 0 ? xb[v] : -xb[v];
+                }
+                if (bad) {
+#pragma omp atomic write
+                    status = -1;
+                    continue;
+                }
+                double wc = w ? w[c] : 1.0;
+                double fe = orc_fe(type[c], param[c], Lc, y, dy);
+                acc += wc * fabs(fe);
+                double fl = ((floor_types >> type[c]) & 1) ? floor : 0.0;
+                for (int i = 0; i < Lc; ++i) {
+                    int32_t lit = lits[a + i];
+                    int32_t v = (lit > 0 ? lit : -lit) - 1;
+                    double d = fabs(dy[i]);
+                    Ab[v] += wc * (d > fl ? d : fl);
+                }
+            }
+            sf[b] = acc;
+        }
+        free(y);
+        free(dy);
+    }
+    return status;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Exact checker twin                                                       */
 /* ------------------------------------------------------------------------ */

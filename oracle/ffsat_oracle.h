@@ -89,6 +89,15 @@ int orc_eval_grad(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *l
                   const uint8_t *type, const int32_t *param, const double *w,
                   int32_t B, const double *x, double *f, double *g, int nthreads, int route);
 
+/* Condition scales of the sums above, used for tolerances: sf[b] = sum_c w_c |FE_c(x_b)|
+ * and A[b, v] = sum_{c contains v} w_c max(|dFE_c/dy_v|, floor_c), where floor_c =
+ * floor for constraints whose type bit is set in floor_types (bit t for type t)
+ * and 0 otherwise.  Returns 0 or -1. */
+int orc_eval_scale(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *lits,
+                   const uint8_t *type, const int32_t *param, const double *w,
+                   int32_t B, const double *x, double *sf, double *A, double floor, int floor_types,
+                   int nthreads);
+
 /* Exact checker twin (Alg. 1, line 5, read as an exact test): z = sgn(x) with
  * sgn(x) = -1 iff x < 0 (so +-0 -> +1); every constraint is evaluated on z with
  * integer counting; n_unsat[b] = number of violated constraints, sat[b] = (n_unsat == 0).

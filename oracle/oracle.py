@@ -48,6 +48,9 @@ def lib():
         L.orc_paper_ftilde.restype = None
         L.orc_eval_grad.argtypes = [C.c_int32, C.c_int32, _i64, _i32, _u8, _i32, _dp, C.c_int32, _dp, _dp, _dp, C.c_int, C.c_int]
         L.orc_eval_grad.restype = C.c_int
+        L.orc_eval_scale.argtypes = [C.c_int32, C.c_int32, _i64, _i32, _u8, _i32, _dp, C.c_int32, _dp, _dp, _dp,
+                                     C.c_double, C.c_int, C.c_int]
+        L.orc_eval_scale.restype = C.c_int
         L.orc_check.argtypes = [C.c_int32, C.c_int32, _i64, _i32, _u8, _i32, C.c_int32, _dp, _u8, _i32, C.c_int]
         L.orc_check.restype = C.c_int
         L.orc_splitmix64.argtypes = [C.c_uint64]
@@ -157,6 +160,24 @@ def eval_grad(inst, x, nthreads: int = 0, route: str = "default", weights=None):
     if rc != 0:
         raise ValueError("oracle: bad input (variable out of range or NaN)")
     return f, g
+
+
+def eval_scale(inst, x, floor: float = 0.0, nthreads: int = 0, weights=None, floor_types=(ATLEAST,)):
+    """Condition scales (sum_c w|FE_c|, A[b,v] = sum_{c ni v} w max(|dFE_c/dy_v|, floor)) at x;
+    the floor applies to constraints whose type is in floor_types."""
+    rp, lits, ty, pa, w = _inst_arrays(inst)
+    if weights is not None:
+        w = _f64(weights)
+    x = _f64(np.atleast_2d(x))
+    B = x.shape[0]
+    sf = np.zeros(B)
+    A = np.zeros_like(x)
+    rc = lib().orc_eval_scale(inst.n, inst.m, _p(rp, _i64), _p(lits, _i32), _p(ty, _u8), _p(pa, _i32), _p(w, _dp),
+                              B, _p(x, _dp), _p(sf, _dp), _p(A, _dp), float(floor),
+                              sum(1 << t for t in floor_types), nthreads)
+    if rc != 0:
+        raise ValueError("oracle: bad input")
+    return sf, A
 
 
 def check(inst, x, nthreads: int = 0):

@@ -1,0 +1,1018 @@
+// Host side of libffsat: validation, FP64 preprocessing of the node tables,
+// length bucketing, device upload and the C ABI declared in include/ffsat.h.
+#include <algorithm>
+#include <array>
+#include <functional>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "ffsat.h"
+#include "ffsat_internal.h"
+
+using namespace ffsat;
+
+namespace {
+
+thread_local std::string t_err;
+thread_local int32_t t_launches = 0;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess) return fail(FFSAT_ERR_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr int kMaxLen = FFSAT_MAX_LEN;
+constexpr int kPaperMaxLen = 60;
+
+enum ConsClass : int8_t { CLS_CLAUSE3 = 0, CLS_PRODUCT = 1, CLS_NODE = 2, CLS_CONST = 3 };
+
+// v(s) of a symmetric constraint: -1 if s True literals satisfy it, +1 otherwise.
+inline int truth_value(int type, int param, int s) {
+    if (type == FFSAT_OR) return s >= 1 ? -1 : 1;
+    if (type == FFSAT_XOR) return ((s & 1) == (param & 1)) ? -1 : 1;
+    return s >= param ? -1 : 1;
+}
+
+inline int pow2_at_least(int v) {
+    int g = 1;
+    while (g < v) g <<= 1;
+    return g;
+}
+
+// Walsh coefficients a_m (coefficient of e_m in the expansion, Eq. effi_eval)
+// of a symmetric constraint with L <= 60 literals.  Setting every literal to
+// the same value t turns the expansion into sum_m a_m C(L,m) t^m, while the
+// probability reading gives 2^-L sum_s v(s) C(L,s) (1-t)^s (1+t)^(L-s); the
+// coefficients of the latter polynomial are computed in exact 128-bit integers.
+void walsh_coefficients(int type, int param, int L, std::vector<double> &a) {
+    std::vector<std::vector<__int128>> C(L + 1, std::vector<__int128>(L + 1, 0));
+    for (int i = 0; i <= L; ++i) {
+        C[i][0] = 1;
+        for (int k = 1; k <= i; ++k) C[i][k] = C[i - 1][k - 1] + (k < i ? C[i - 1][k] : 0);
+    }
+    std::vector<__int128> Q(L + 1, 0);
+    std::vector<__int128> poly(L + 1);
+    for (int s = 0; s <= L; ++s) {
+        // poly = (1 - t)^s (1 + t)^(L - s)
+        std::fill(poly.begin(), poly.end(), 0);
+        poly[0] = 1;
+        int deg = 0;
+        for (int k = 0; k < L; ++k) {
+            const __int128 sg = k < s ? -1 : 1;
+            for (int d = deg + 1; d >= 1; --d) poly[d] += sg * poly[d - 1];
+            ++deg;
+        }
+        const __int128 scale = C[L][s] * (__int128)truth_value(type, param, s);
+        for (int d = 0; d <= L; ++d) Q[d] += scale * poly[d];
+    }
+    a.assign(L + 1, 0.0);
+    for (int m = 0; m <= L; ++m)
+        a[m] = std::ldexp((double)Q[m] / (double)C[L][m], -L);
+}
+
+// Split alpha_re + beta_re = 1 so that the rounded pair still sums to exactly 1
+// (then the padding value y = +1 gives a factor of exactly 1 + 0i).
+template <typename R>
+void split_unit(double alpha, R &a, R &b) {
+    if (alpha >= 0.5) {
+        a = (R)alpha;
+        b = R(1) - a;
+    } else {
+        b = (R)(1.0 - alpha);
+        a = R(1) - b;
+    }
+}
+
+struct Arena {
+    std::vector<unsigned char> host;
+    template <typename T>
+    size_t put(const std::vector<T> &v) {
+        size_t off = (host.size() + 255) & ~size_t(255);
+        host.resize(off + std::max<size_t>(v.size() * sizeof(T), 16));
+        if (!v.empty()) std::memcpy(host.data() + off, v.data(), v.size() * sizeof(T));
+        return off;
+    }
+};
+
+struct TaskSet {
+    std::vector<int4> tasks;
+    int node_r = 0;
+};
+
+}  // namespace
+
+struct ffsat_instance {
+    int device = 0;
+    int32_t n = 0, m = 0;
+    int64_t nnz = 0;
+    ffsat_options opt{};
+    int num_sms = 0;
+    int max_smem = 0;
+    // per constraint
+    std::vector<int8_t> cls;
+    std::vector<int32_t> slot;
+    std::vector<double> w;
+    std::vector<uint8_t> type;
+    std::vector<int32_t> param, len;
+    // host copies of the weight-carrying arrays
+    std::vector<int4> clauses;   // {l0, l1, l2, FP32 weight bits}, bank-ordered, padded
+    std::vector<int4> seg_info;  // canonical {offset into seg_lits, length, aux, FP32 weight bits}
+    std::vector<int32_t> seg_lits;
+    int n_node_seg = 0;
+    int32_t pad_node = 0;        // padding literal of node segments (dummy n or n + 1)
+    int nr[2] = {0, 0};          // node R of image 0 (FP32) and image 1 (FP64)
+    std::vector<double> clause_wd;
+    std::vector<double> seg_wd;
+    std::vector<double> cons_wd;
+    double f_const = 0.0;        // constants of the fused kernel's f (see fill_weights)
+    double f_const_plain = 0.0;  // sum of w FE over constant constraints
+    float fix_s1 = 1.0f, fix_s2 = 1.0f, fix_i1 = 1.0f, fix_i12 = 1.0f;
+    std::vector<int64_t> row_ptr;  // host copy of the CSR (fixed-point scales)
+    std::vector<int32_t> lits_in;
+    // resident images per dtype (index 0: FP32 task list, 1: FP64 task list)
+    std::vector<int4> tasks[2];
+    std::vector<int4> image[2];
+    int32_t img_off[2][4] = {{0}};  // tasks, clauses, segmeta, seg_lits (int4 units)
+    size_t off_image[2] = {0, 0};
+    // device
+    unsigned char *d_arena = nullptr;
+    size_t arena_bytes = 0;
+    size_t off_clause_wd = 0, off_seg_wd = 0, off_cons_wd = 0;
+    int32_t *d_status = nullptr;
+    int32_t *d_node_ids = nullptr, *d_closed_ids = nullptr;
+    int32_t n_node_ids = 0, n_closed_ids = 0;
+    DevView V32{}, V64{};
+    int nr32 = 0, nr64 = 0;
+    int smem_mode32 = SMEM_FULL, smem_mode64 = SMEM_FULL;
+    size_t smem32 = 0, smem64 = 0;
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    ffsat_info info{};
+};
+
+namespace {
+
+int validate(int32_t n, int32_t m, const int64_t *rp, const int32_t *lits, const uint8_t *type,
+             const int32_t *param, const double *w, const ffsat_options &o) {
+    if (n <= 0) return fail(FFSAT_ERR_ARG, "n_vars must be positive (got %d)", n);
+    if (m < 0) return fail(FFSAT_ERR_ARG, "n_cons must be >= 0 (got %d)", m);
+    if (o.form != FFSAT_FORM_STABLE && o.form != FFSAT_FORM_PAPER) return fail(FFSAT_ERR_ARG, "bad form %d", o.form);
+    if (o.node_r != 0 && o.node_r != 8 && o.node_r != 16) return fail(FFSAT_ERR_ARG, "node_r must be 0, 8 or 16");
+    if (!rp) return fail(FFSAT_ERR_ARG, "row_ptr is NULL");
+    if (m > 0 && (!type || !param)) return fail(FFSAT_ERR_ARG, "type/param is NULL");
+    if (rp[0] != 0) return fail(FFSAT_ERR_PARAM, "row_ptr[0] must be 0");
+    const int64_t nnz = rp[m];
+    if (nnz < 0 || nnz >= (int64_t(1) << 31) - 1) return fail(FFSAT_ERR_ARG, "literal count out of range");
+    if (nnz > 0 && !lits) return fail(FFSAT_ERR_ARG, "lits is NULL");
+    std::vector<int32_t> stamp((size_t)n, -1);
+    for (int32_t c = 0; c < m; ++c) {
+        const int64_t a = rp[c], e = rp[c + 1];
+        if (e < a || e > nnz) return fail(FFSAT_ERR_PARAM, "row_ptr not non-decreasing at constraint %d", c);
+        const int64_t L = e - a;
+        if (L == 0) return fail(FFSAT_ERR_EMPTY, "constraint %d has no literals", c);
+        if (L > kMaxLen) return fail(FFSAT_ERR_TOOLONG, "constraint %d has %lld literals (max %d)", c, (long long)L, kMaxLen);
+        const int t = type[c];
+        if (t != FFSAT_OR && t != FFSAT_XOR && t != FFSAT_ATLEAST) return fail(FFSAT_ERR_PARAM, "constraint %d: unknown type %d", c, t);
+        if (t == FFSAT_XOR && param[c] != 0 && param[c] != 1) return fail(FFSAT_ERR_PARAM, "constraint %d: XOR parity must be 0 or 1", c);
+        if (t == FFSAT_ATLEAST && param[c] < 0) return fail(FFSAT_ERR_PARAM, "constraint %d: K must be >= 0", c);
+        if (w && !(std::isfinite(w[c]) && w[c] >= 0.0)) return fail(FFSAT_ERR_WEIGHT, "constraint %d: weight must be finite and >= 0", c);
+        for (int64_t i = a; i < e; ++i) {
+            const int32_t l = lits[i];
+            if (l == 0 || l == INT32_MIN) return fail(FFSAT_ERR_VAR_RANGE, "constraint %d: literal %d", c, l);
+            const int32_t v = (l > 0 ? l : -l) - 1;
+            if (v >= n) return fail(FFSAT_ERR_VAR_RANGE, "constraint %d: variable %d > n_vars", c, v + 1);
+            if (stamp[v] == c) return fail(FFSAT_ERR_DUPVAR, "constraint %d: variable %d occurs twice", c, v + 1);
+            stamp[v] = c;
+        }
+    }
+    return FFSAT_OK;
+}
+
+// Packed literal: variable index | (negated << 31).
+inline int32_t pack_lit(int32_t l) {
+    const uint32_t v = (uint32_t)((l > 0 ? l : -l) - 1);
+    return (int32_t)(v | (l < 0 ? 0x80000000u : 0u));
+}
+
+// Lanes per constraint segment: the smallest power of two G with G * R >= L.
+inline int seg_lanes(int L, int R) { return std::max(1, pow2_at_least((L + R - 1) / R)); }
+
+// Per-constraint FE of constant constraints (cardinality with K <= 0 or K > L).
+inline bool constant_value(int type, int param, int L, double &fe) {
+    if (type != FFSAT_ATLEAST) return false;
+    if (param <= 0) {
+        fe = -1.0;
+        return true;
+    }
+    if (param > L) {
+        fe = 1.0;
+        return true;
+    }
+    return false;
+}
+
+// Append the node table of one (type, L, param) key: J = floor((L+1)/2) + 1
+// nodes of the N = L + 1 roots of unity, conjugate-symmetric half with the
+// multiplicity folded into c_j and d_j.
+void build_table(int type, int param, int L, int form, std::vector<float> &tf, std::vector<double> &td) {
+    const int N = L + 1;
+    const int J = N / 2 + 1;
+    std::vector<double> coef(L + 1);
+    if (form == FFSAT_FORM_PAPER) {
+        walsh_coefficients(type, param, L, coef);  // coefficient of e_m
+    } else {
+        for (int s = 0; s <= L; ++s) coef[s] = (double)truth_value(type, param, s);  // v(s)
+    }
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    for (int j = 0; j < J; ++j) {
+        const double mult = (j == 0 || 2 * j == N) ? 1.0 : 2.0;
+        const double th = -two_pi * (double)j / (double)N;  // omega^j = exp(i th)
+        const double wr = std::cos(th), wi = std::sin(th);
+        double ar, ai, br, bi;
+        if (form == FFSAT_FORM_PAPER) {
+            ar = 1.0;
+            ai = 0.0;
+            br = wr;
+            bi = wi;
+        } else {
+            ar = 0.5 * (1.0 + wr);
+            ai = 0.5 * wi;
+            br = 0.5 * (1.0 - wr);
+            bi = -0.5 * wi;
+        }
+        // c_j = (mult / N) sum_k coef[k] omega^{-j k}
+        double cr = 0.0, ci = 0.0;
+        for (int k = 0; k <= L; ++k) {
+            const long long jk = ((long long)j * k) % N;
+            const double ph = two_pi * (double)jk / (double)N;
+            cr += coef[k] * std::cos(ph);
+            ci += coef[k] * std::sin(ph);
+        }
+        cr *= mult / N;
+        ci *= mult / N;
+        const double dr = cr * br - ci * bi, di = cr * bi + ci * br;
+        // FP32 entry
+        float far, fbr;
+        if (form == FFSAT_FORM_PAPER) {
+            far = 1.0f;
+            fbr = (float)br;
+        } else {
+            split_unit<float>(ar, far, fbr);
+        }
+        const float fai = (float)ai;
+        const float fbi = form == FFSAT_FORM_PAPER ? (float)bi : -fai;
+        const float ft[8] = {far, fai, fbr, fbi, (float)dr, (float)di, (float)cr, (float)ci};
+        tf.insert(tf.end(), ft, ft + 8);
+        double dar, dbr;
+        if (form == FFSAT_FORM_PAPER) {
+            dar = 1.0;
+            dbr = br;
+        } else {
+            split_unit<double>(ar, dar, dbr);
+        }
+        const double dbi = form == FFSAT_FORM_PAPER ? bi : -ai;
+        const double dt[8] = {dar, ai, dbr, dbi, dr, di, cr, ci};
+        td.insert(td.end(), dt, dt + 8);
+    }
+}
+
+// Warp tasks for one node R: node tasks (longest first), then product tasks,
+// then clause tasks.  Segments are node constraints followed by product
+// constraints, each group sorted by length, descending.
+void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clause, int node_r, TaskSet &ts) {
+    ts.tasks.clear();
+    ts.node_r = node_r;
+    auto group = [&](int first, int count, int kind, int R) {
+        int i = first;
+        const int end = first + count;
+        while (i < end) {
+            const int L = seg_len[i];
+            const int G = seg_lanes(L, R);
+            const int S = 32 / G;
+            int k = 0;
+            while (k < S && i + k < end) {
+                if (seg_lanes(seg_len[i + k], R) != G) break;
+                ++k;
+            }
+            const int J = kind == TASK_NODE ? (L + 1) / 2 + 1 : 0;
+            ts.tasks.push_back(make_int4(kind | (G << 8), i, k, J));
+            i += k;
+        }
+    };
+    if (n_node_seg > 0) group(0, n_node_seg, TASK_NODE, node_r);
+    group(n_node_seg, (int)seg_len.size() - n_node_seg, TASK_PROD, kProdR);
+    const int per = 32 * kClausePerLane;  // the clause list is padded to a multiple of this
+    for (int c = 0; c < n_clause; c += per) ts.tasks.push_back(make_int4(TASK_CLAUSE, c, per, 0));
+}
+
+int smem_mode_for(int n, size_t elem, size_t image_bytes, int max_smem, size_t &bytes) {
+    const size_t npad = ((size_t)n + 2 + 3) & ~size_t(3);  // two dummy variables, rounded to 4
+    const size_t budget = max_smem > 2048 ? (size_t)max_smem - 1024 : 0;
+    // FP32 resident mode keeps the gradient as two int32 words and one FP32 word per variable
+    const size_t res_xg = elem == 4 ? 4 * npad * 4 : 2 * npad * elem;
+    if (res_xg + image_bytes <= budget) {
+        bytes = res_xg + image_bytes;
+        return SMEM_RES;
+    }
+    if (2 * npad * elem <= budget) {
+        bytes = 2 * npad * elem;
+        return SMEM_FULL;
+    }
+    if (npad * elem <= budget) {
+        bytes = npad * elem;
+        return SMEM_X;
+    }
+    bytes = 0;
+    return SMEM_NONE;
+}
+
+using FusedFn = cudaError_t (*)(const DevView &, int, const FusedArgs &, size_t, int, cudaStream_t, bool);
+
+FusedFn launcher_for(bool f64, int nr) {
+    if (f64) return nr == 0 ? fused_f64_r0 : (nr == 8 ? fused_f64_r8 : fused_f64_r16);
+    return nr == 0 ? fused_f32_r0 : (nr == 8 ? fused_f32_r8 : fused_f32_r16);
+}
+
+// Scales of the two-word fixed-point accumulator: a contribution is bounded by
+// its weight (|dFE/dy| <= 1, with a margin for rounding), so with S1 =
+// min(21 - ceil(log2 wmax), 30 - ceil(log2 Dmax)) the hi word is rounded
+// exactly (|c 2^S1| < 2^22) and never exceeds 2^30 in sum (Dmax = largest
+// weighted variable degree); the residual lies in [-1/2, 1/2], so with
+// S2 = min(22, 30 - ceil(log2 degmax)) the lo word is exact and bounded too.
+void fixed_point_scales(ffsat_instance *I) {
+    std::vector<double> D((size_t)I->n, 0.0);
+    std::vector<int32_t> deg((size_t)I->n, 0);
+    double wmax = 0.0;
+    for (int32_t c = 0; c < I->m; ++c) {
+        if (I->cls[c] == CLS_CONST) continue;
+        wmax = std::max(wmax, I->w[c]);
+        for (int64_t i = I->row_ptr[c]; i < I->row_ptr[c + 1]; ++i) {
+            const int32_t l = I->lits_in[i];
+            const int32_t v = (l > 0 ? l : -l) - 1;
+            D[v] += I->w[c];
+            deg[v] += 1;
+        }
+    }
+    double dmax = 0.0;
+    int32_t gmax = 1;
+    for (int32_t v = 0; v < I->n; ++v) {
+        dmax = std::max(dmax, D[v]);
+        gmax = std::max(gmax, deg[v]);
+    }
+    if (wmax <= 0.0) wmax = 1.0;
+    if (dmax <= 0.0) dmax = 1.0;
+    const int e_w = (int)std::ceil(std::log2(wmax * 1.0625));
+    const int e_d = (int)std::ceil(std::log2(dmax * 1.0625 + 1.0));
+    const int S1 = std::min(21 - e_w, 30 - e_d);
+    const int S2 = std::min(22, 30 - (int)std::ceil(std::log2((double)gmax + 1.0)));
+    I->fix_s1 = std::ldexp(1.0f, S1);
+    I->fix_s2 = std::ldexp(1.0f, S2);
+    I->fix_i1 = std::ldexp(1.0f, -S1);
+    I->fix_i12 = std::ldexp(1.0f, -(S1 + S2));
+}
+
+void fill_weights(ffsat_instance *I) {
+    fixed_point_scales(I);
+    I->f_const = 0.0;
+    I->f_const_plain = 0.0;
+    for (int32_t c = 0; c < I->m; ++c) {
+        const double wc = I->w[c];
+        I->cons_wd[c] = wc;
+        const int s = I->slot[c];
+        switch (I->cls[c]) {
+        case CLS_CLAUSE3: {
+            const float wf = (float)wc;
+            std::memcpy(&I->clauses[s].w, &wf, 4);
+            I->clause_wd[s] = wc;
+            I->f_const -= wc;  // the kernel accumulates 2 w prod q; FE = 2 prod q - 1
+            break;
+        }
+        case CLS_PRODUCT:
+        case CLS_NODE: {
+            const float wf = (float)wc;
+            std::memcpy(&I->seg_info[s].w, &wf, 4);
+            I->seg_wd[s] = wc;
+            break;
+        }
+        default: {
+            double fe = 0.0;
+            constant_value(I->type[c], I->param[c], I->len[c], fe);
+            I->f_const += wc * fe;
+            I->f_const_plain += wc * fe;
+        }
+        }
+    }
+}
+
+// Image k = {tasks | clauses | segmeta | segment literals}, each part 16-byte
+// aligned.  Segment s of length L on lanes G = seg_lanes(L, R) occupies G * R
+// literal slots; lane sl reads slots [sl R, sl R + R).  Unused slots hold the
+// padding literal (dummy variable n, or n + 1 for paper-form node factors).
+void build_image(ffsat_instance *I, int k) {
+    const int nr = I->nr[k];
+    std::vector<int4> meta(I->seg_info.size());
+    std::vector<int32_t> lits;
+    for (size_t s = 0; s < I->seg_info.size(); ++s) {
+        const int4 si = I->seg_info[s];
+        const bool node = (int)s < I->n_node_seg;
+        const int R = node ? nr : kProdR;
+        const int G = seg_lanes(si.y, R);
+        const int32_t pad = node ? I->pad_node : I->n;
+        const int32_t off = (int32_t)lits.size();
+        lits.insert(lits.end(), I->seg_lits.begin() + si.x, I->seg_lits.begin() + si.x + si.y);
+        lits.resize((size_t)off + (size_t)G * R, pad);
+        meta[s] = make_int4(off, si.y, si.z, si.w);
+    }
+    std::vector<int4> &img = I->image[k];
+    img.clear();
+    I->img_off[k][0] = (int32_t)img.size();
+    img.insert(img.end(), I->tasks[k].begin(), I->tasks[k].end());
+    I->img_off[k][1] = (int32_t)img.size();
+    img.insert(img.end(), I->clauses.begin(), I->clauses.end());
+    I->img_off[k][2] = (int32_t)img.size();
+    img.insert(img.end(), meta.begin(), meta.end());
+    I->img_off[k][3] = (int32_t)img.size();
+    const size_t nl = lits.size();
+    const size_t base = img.size();
+    img.resize(base + (nl + 3) / 4, make_int4(I->n, I->n, I->n, I->n));
+    if (nl) std::memcpy(reinterpret_cast<int32_t *>(img.data() + base), lits.data(), nl * sizeof(int32_t));
+}
+
+// Order clauses in groups of 32 (one per warp instruction) so that, literal
+// position by literal position, the 32 variables of a group fall into distinct
+// shared-memory banks (bank = variable mod 32).  A group is conflict-free iff
+// every bank occurs exactly 3 times among its 96 literals: its clause-bank
+// incidence graph is then 3-regular bipartite and splits into 3 perfect
+// matchings (one per literal position).  Packing: best fit of each clause into
+// the fullest group that still has capacity 3 per bank, leftovers where they
+// exceed the capacity least; positions: one maximum matching per position.
+void bank_order(std::vector<int4> &cls, std::vector<int32_t> &cid) {
+    const size_t m = cls.size();
+    if (m == 0) return;
+    const size_t G = (m + 31) / 32;
+    std::vector<std::array<uint8_t, 32>> cap(G);
+    for (auto &c : cap) c.fill(3);
+    std::vector<int> size(G, 0);
+    std::vector<std::vector<int32_t>> members(G);
+    auto banks = [&](size_t i) {
+        const int4 &c = cls[i];
+        return std::array<int, 3>{(int)((uint32_t)c.x & 31u), (int)((uint32_t)c.y & 31u), (int)((uint32_t)c.z & 31u)};
+    };
+    // groups with free slots, kept ordered by size (fullest first) through buckets
+    std::vector<std::vector<int32_t>> by_size(33);
+    for (size_t g = 0; g < G; ++g) by_size[0].push_back((int32_t)g);
+    std::vector<int32_t> where(G, 0);  // index of g inside by_size[size[g]]
+    for (size_t g = 0; g < G; ++g) where[g] = (int32_t)g;
+    auto move_group = [&](int32_t g, int from, int to) {
+        auto &vf = by_size[from];
+        const int32_t last = vf.back();
+        vf[where[g]] = last;
+        where[last] = where[g];
+        vf.pop_back();
+        where[g] = (int32_t)by_size[to].size();
+        by_size[to].push_back(g);
+    };
+    std::vector<int32_t> left;
+    for (size_t i = 0; i < m; ++i) {
+        const auto b = banks(i);
+        int found = -1;
+        for (int sz = 31; sz >= 0 && found < 0; --sz) {
+            for (int32_t g : by_size[sz]) {
+                uint8_t need[32] = {0};
+                bool ok = true;
+                for (int q = 0; q < 3 && ok; ++q) ok = cap[g][b[q]] > need[b[q]]++;
+                if (ok) {
+                    found = g;
+                    break;
+                }
+            }
+        }
+        if (found < 0) {
+            left.push_back((int32_t)i);
+            continue;
+        }
+        for (int q = 0; q < 3; ++q) cap[found][b[q]]--;
+        members[found].push_back((int32_t)i);
+        move_group(found, size[found], size[found] + 1);
+        size[found]++;
+    }
+    for (int32_t i : left) {
+        const auto b = banks(i);
+        int best = -1, best_cost = 1 << 30;
+        for (size_t g = 0; g < G; ++g) {
+            if (size[g] >= 32) continue;
+            int cost = 0;
+            uint8_t need[32] = {0};
+            for (int q = 0; q < 3; ++q) cost += cap[g][b[q]] > need[b[q]]++ ? 0 : 1;
+            if (cost < best_cost) {
+                best_cost = cost;
+                best = (int)g;
+            }
+        }
+        for (int q = 0; q < 3; ++q) cap[best][b[q]] = cap[best][b[q]] ? cap[best][b[q]] - 1 : 0;
+        members[best].push_back(i);
+        size[best]++;
+    }
+    // literal positions by maximum bipartite matching (clauses x banks), position by position
+    std::vector<int4> out;
+    std::vector<int32_t> out_id;
+    out.reserve(G * 32);
+    out_id.reserve(G * 32);
+    for (size_t g = 0; g < G; ++g) {
+        const auto &mem = members[g];
+        const int k = (int)mem.size();
+        std::vector<std::array<int32_t, 3>> lit(k);
+        std::vector<std::array<bool, 3>> used(k);
+        std::vector<std::array<int32_t, 3>> pos(k);
+        for (int c = 0; c < k; ++c) {
+            const int4 &r = cls[mem[c]];
+            lit[c] = {r.x, r.y, r.z};
+            used[c] = {false, false, false};
+        }
+        for (int q = 0; q < 3; ++q) {
+            int owner_c[32], owner_k[32];
+            std::fill(owner_c, owner_c + 32, -1);
+            std::function<bool(int, uint32_t &)> augment = [&](int c, uint32_t &seen) -> bool {
+                for (int t = 0; t < 3; ++t) {
+                    if (used[c][t]) continue;
+                    const int bk = (int)((uint32_t)lit[c][t] & 31u);
+                    if (seen & (1u << bk)) continue;
+                    seen |= 1u << bk;
+                    if (owner_c[bk] < 0 || augment(owner_c[bk], seen)) {
+                        owner_c[bk] = c;
+                        owner_k[bk] = t;
+                        return true;
+                    }
+                }
+                return false;
+            };
+            for (int c = 0; c < k; ++c) {
+                uint32_t seen = 0;
+                augment(c, seen);
+            }
+            std::vector<int> chosen(k, -1);
+            for (int bk = 0; bk < 32; ++bk)
+                if (owner_c[bk] >= 0) chosen[owner_c[bk]] = owner_k[bk];
+            for (int c = 0; c < k; ++c) {
+                int t = chosen[c];
+                if (t < 0)
+                    for (t = 0; used[c][t]; ++t) {
+                    }
+                used[c][t] = true;
+                pos[c][q] = lit[c][t];
+            }
+        }
+        for (int c = 0; c < k; ++c) {
+            out.push_back(make_int4(pos[c][0], pos[c][1], pos[c][2], cls[mem[c]].w));
+            out_id.push_back(cid[mem[c]]);
+        }
+    }
+    cls.swap(out);
+    cid.swap(out_id);
+}
+
+}  // namespace
+
+extern "C" {
+
+void ffsat_default_options(ffsat_options *opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->form = FFSAT_FORM_STABLE;
+    opt->node_all = 0;
+    opt->node_r = 0;
+    opt->autotune = 0;
+    opt->device = -1;
+}
+
+const char *ffsat_last_error(void) { return t_err.c_str(); }
+
+int32_t ffsat_last_launch_count(void) { return t_launches; }
+
+int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, const int32_t *lits,
+                        const uint8_t *type, const int32_t *param, const double *weights,
+                        const ffsat_options *opt_in, ffsat_instance **out) {
+    t_err.clear();
+    if (!out) return fail(FFSAT_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    ffsat_options opt;
+    ffsat_default_options(&opt);
+    if (opt_in) opt = *opt_in;
+    int rc = validate(n_vars, n_cons, row_ptr, lits, type, param, weights, opt);
+    if (rc != FFSAT_OK) return rc;
+
+    std::unique_ptr<ffsat_instance> I(new ffsat_instance());
+    ffsat_instance *P = I.get();
+    P->n = n_vars;
+    P->m = n_cons;
+    P->nnz = row_ptr[n_cons];
+    P->opt = opt;
+    P->cls.resize(n_cons);
+    P->slot.resize(n_cons);
+    P->w.resize(n_cons);
+    P->type.assign(type, type + n_cons);
+    P->param.assign(param, param + n_cons);
+    P->len.resize(n_cons);
+    P->cons_wd.resize(n_cons);
+    P->row_ptr.assign(row_ptr, row_ptr + n_cons + 1);
+    P->lits_in.assign(lits, lits + P->nnz);
+
+    // ---- classify ----
+    std::vector<int32_t> node_c, prod_c, clause_c, const_c;
+    for (int32_t c = 0; c < n_cons; ++c) {
+        const int L = (int)(row_ptr[c + 1] - row_ptr[c]);
+        P->len[c] = L;
+        P->w[c] = weights ? weights[c] : 1.0;
+        const int t = type[c];
+        double fe;
+        if (constant_value(t, param[c], L, fe)) {
+            P->cls[c] = CLS_CONST;
+            const_c.push_back(c);
+        } else if (!opt.node_all && t == FFSAT_OR && L <= 3) {
+            P->cls[c] = CLS_CLAUSE3;
+            clause_c.push_back(c);
+        } else if (!opt.node_all && t != FFSAT_ATLEAST && L <= 32 * kProdR) {
+            P->cls[c] = CLS_PRODUCT;
+            prod_c.push_back(c);
+        } else {
+            if (opt.form == FFSAT_FORM_PAPER && L > kPaperMaxLen)
+                return fail(FFSAT_ERR_TOOLONG, "paper form supports constraints of <= %d literals (constraint %d has %d)",
+                            kPaperMaxLen, c, L);
+            P->cls[c] = CLS_NODE;
+            node_c.push_back(c);
+        }
+    }
+    auto by_len_desc = [&](int32_t a, int32_t b) { return P->len[a] > P->len[b] || (P->len[a] == P->len[b] && a < b); };
+    std::stable_sort(node_c.begin(), node_c.end(), by_len_desc);
+    std::stable_sort(prod_c.begin(), prod_c.end(), by_len_desc);
+
+    // ---- node tables (one per distinct key), FP64 preprocessing ----
+    std::map<std::tuple<int, int, int>, int32_t> tab_index;
+    std::vector<float> tab_f;
+    std::vector<double> tab_d;
+    std::vector<int32_t> cons_tab(n_cons, -1);
+    int max_node_len = 0;
+    for (int32_t c : node_c) {
+        const int L = P->len[c];
+        const int t = type[c];
+        const int p = t == FFSAT_OR ? 0 : (t == FFSAT_XOR ? (param[c] & 1) : param[c]);
+        auto key = std::make_tuple(t, L, p);
+        auto it = tab_index.find(key);
+        if (it == tab_index.end()) {
+            const int32_t off = (int32_t)(tab_f.size() / 8);
+            build_table(t, p, L, opt.form, tab_f, tab_d);
+            it = tab_index.emplace(key, off).first;
+        }
+        cons_tab[c] = it->second;
+        max_node_len = std::max(max_node_len, L);
+    }
+
+    // ---- segments, clauses, CSR ----
+    std::vector<int32_t> seg_len;
+    std::vector<int32_t> &seg_lits = P->seg_lits;
+    auto add_seg = [&](int32_t c, int32_t aux) {
+        P->slot[c] = (int32_t)seg_len.size();
+        P->seg_info.push_back(make_int4((int32_t)seg_lits.size(), P->len[c], aux, 0));
+        seg_len.push_back(P->len[c]);
+        for (int64_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) seg_lits.push_back(pack_lit(lits[i]));
+    };
+    for (int32_t c : node_c) add_seg(c, cons_tab[c]);
+    for (int32_t c : prod_c) {
+        const int t = type[c];
+        add_seg(c, t == FFSAT_OR ? PROD_OR : ((param[c] & 1) ? PROD_XOR_ODD : PROD_XOR_EVEN));
+    }
+    P->n_node_seg = (int)node_c.size();
+    P->pad_node = opt.form == FFSAT_FORM_PAPER ? n_vars + 1 : n_vars;
+    P->seg_wd.assign(seg_len.size(), 0.0);
+    // clauses of <= 3 literals: bank-ordered, then padded to whole tasks with
+    // zero-weight clauses on the dummy variable
+    std::vector<int32_t> clause_ids = clause_c;
+    P->clauses.resize(clause_c.size());
+    for (size_t k = 0; k < clause_c.size(); ++k) {
+        const int32_t c = clause_c[k];
+        int32_t l3[3] = {n_vars, n_vars, n_vars};
+        for (int64_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) l3[i - row_ptr[c]] = pack_lit(lits[i]);
+        P->clauses[k] = make_int4(l3[0], l3[1], l3[2], 0);
+    }
+    bank_order(P->clauses, clause_ids);
+    const size_t per_task = 32 * kClausePerLane;
+    const size_t n_clause_pad = (clause_ids.size() + per_task - 1) / per_task * per_task;
+    P->clauses.resize(n_clause_pad, make_int4(n_vars, n_vars, n_vars, 0));
+    P->clause_wd.assign(n_clause_pad, 0.0);
+    for (size_t k = 0; k < clause_ids.size(); ++k) P->slot[clause_ids[k]] = (int32_t)k;
+    for (int32_t c : const_c) P->slot[c] = -1;
+    fill_weights(P);
+
+    std::vector<int32_t> rp32(n_cons + 1), lp32((size_t)P->nnz);
+    for (int32_t c = 0; c <= n_cons; ++c) rp32[c] = (int32_t)row_ptr[c];
+    for (int64_t i = 0; i < P->nnz; ++i) lp32[i] = pack_lit(lits[i]);
+    std::vector<int32_t> par32(param, param + n_cons);
+    std::vector<int32_t> closed_ids;
+    closed_ids.insert(closed_ids.end(), clause_c.begin(), clause_c.end());
+    closed_ids.insert(closed_ids.end(), prod_c.begin(), prod_c.end());
+
+    // ---- node R and task lists ----
+    int nr32 = 0, nr64 = 0;
+    if (!node_c.empty()) {
+        nr32 = opt.node_r ? opt.node_r : 16;
+        if (nr32 * 32 < max_node_len) nr32 = 16;
+        nr64 = max_node_len <= 8 * 32 ? 8 : 16;
+    }
+    P->nr[0] = nr32;
+    P->nr[1] = nr64;
+    TaskSet ts32, ts64;
+    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, nr32, ts32);
+    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, nr64, ts64);
+    P->tasks[0] = ts32.tasks;
+    P->tasks[1] = ts64.tasks;
+    build_image(P, 0);
+    build_image(P, 1);
+
+    // ---- device ----
+    int dev = opt.device;
+    if (dev < 0) CUDA_TRY(cudaGetDevice(&dev));
+    CUDA_TRY(cudaSetDevice(dev));
+    P->device = dev;
+    CUDA_TRY(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
+    CUDA_TRY(cudaDeviceGetAttribute(&P->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+
+    Arena A;
+    P->off_image[0] = A.put(P->image[0]);
+    P->off_image[1] = A.put(P->image[1]);
+    P->off_clause_wd = A.put(P->clause_wd);
+    P->off_seg_wd = A.put(P->seg_wd);
+    const size_t o_tf = A.put(tab_f), o_td = A.put(tab_d);
+    const size_t o_rp = A.put(rp32), o_lits = A.put(lp32), o_type = A.put(P->type), o_par = A.put(par32);
+    const size_t o_ctab = A.put(cons_tab);
+    P->off_cons_wd = A.put(P->cons_wd);
+    const size_t o_nid = A.put(node_c), o_cid = A.put(closed_ids);
+    P->arena_bytes = A.host.size();
+    CUDA_TRY(cudaMalloc(&P->d_arena, P->arena_bytes));
+    CUDA_TRY(cudaMemcpy(P->d_arena, A.host.data(), P->arena_bytes, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMalloc(&P->d_status, sizeof(int32_t)));
+    CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int32_t)));
+
+    unsigned char *base = P->d_arena;
+    DevView V{};
+    V.n = n_vars;
+    V.m = n_cons;
+    V.n_seg = (int32_t)seg_len.size();
+    V.n_clause = (int32_t)n_clause_pad;
+    V.clause_wd = reinterpret_cast<const double *>(base + P->off_clause_wd);
+    V.seg_wd = reinterpret_cast<const double *>(base + P->off_seg_wd);
+    V.tab_f = reinterpret_cast<const float4 *>(base + o_tf);
+    V.tab_d = reinterpret_cast<const double *>(base + o_td);
+    V.pad_y_f = opt.form == FFSAT_FORM_PAPER ? 0.0f : 1.0f;
+    V.pad_y_d = opt.form == FFSAT_FORM_PAPER ? 0.0 : 1.0;
+    V.f_const_d = P->f_const;
+    V.f_const_plain = P->f_const_plain;
+    V.fix_s1 = P->fix_s1;
+    V.fix_s2 = P->fix_s2;
+    V.fix_i1 = P->fix_i1;
+    V.fix_i12 = P->fix_i12;
+    V.f_const_f = (float)P->f_const;
+    V.row_ptr = reinterpret_cast<const int32_t *>(base + o_rp);
+    V.lits = reinterpret_cast<const int32_t *>(base + o_lits);
+    V.type = reinterpret_cast<const uint8_t *>(base + o_type);
+    V.param = reinterpret_cast<const int32_t *>(base + o_par);
+    V.cons_tab = reinterpret_cast<const int32_t *>(base + o_ctab);
+    V.cons_wd = reinterpret_cast<const double *>(base + P->off_cons_wd);
+    V.status = P->d_status;
+    for (int k = 0; k < 2; ++k) {
+        DevView &W = k == 0 ? P->V32 : P->V64;
+        W = V;
+        const int4 *img = reinterpret_cast<const int4 *>(base + P->off_image[k]);
+        W.res_image = img;
+        W.res_int4 = (int32_t)P->image[k].size();
+        W.res_off_tasks = P->img_off[k][0];
+        W.res_off_clauses = P->img_off[k][1];
+        W.res_off_segmeta = P->img_off[k][2];
+        W.res_off_lits = P->img_off[k][3];
+        W.tasks = img + W.res_off_tasks;
+        W.clauses = img + W.res_off_clauses;
+        W.segmeta = img + W.res_off_segmeta;
+        W.seg_lits = reinterpret_cast<const int32_t *>(img + W.res_off_lits);
+        W.n_task = (int32_t)P->tasks[k].size();
+    }
+    P->d_node_ids = reinterpret_cast<int32_t *>(base + o_nid);
+    P->d_closed_ids = reinterpret_cast<int32_t *>(base + o_cid);
+    P->n_node_ids = (int32_t)node_c.size();
+    P->n_closed_ids = (int32_t)closed_ids.size();
+    P->nr32 = nr32;
+    P->nr64 = nr64;
+
+    P->smem_mode32 = smem_mode_for(n_vars, sizeof(float), P->image[0].size() * sizeof(int4), P->max_smem, P->smem32);
+    P->smem_mode64 = smem_mode_for(n_vars, sizeof(double), P->image[1].size() * sizeof(int4), P->max_smem, P->smem64);
+    FusedArgs dummy{};
+    CUDA_TRY(launcher_for(false, nr32)(P->V32, P->smem_mode32, dummy, P->smem32, 0, 0, true));
+    CUDA_TRY(launcher_for(true, nr64)(P->V64, P->smem_mode64, dummy, P->smem64, 0, 0, true));
+
+    ffsat_info &inf = P->info;
+    inf.n = n_vars;
+    inf.m = n_cons;
+    inf.nnz = P->nnz;
+    inf.n_clause3 = (int32_t)clause_c.size();
+    inf.n_product = (int32_t)prod_c.size();
+    inf.n_node = (int32_t)node_c.size();
+    inf.n_const = (int32_t)const_c.size();
+    inf.n_tables = (int32_t)tab_index.size();
+    inf.n_tasks = (int32_t)ts32.tasks.size();
+    inf.node_r = nr32;
+    inf.smem_mode_f32 = P->smem_mode32;
+    inf.smem_mode_f64 = P->smem_mode64;
+    inf.threads_f32 = fused_threads(false, nr32);
+    int64_t lane_work = 0;
+    for (const int4 &t : ts32.tasks)
+        if ((t.x & 0xff) == TASK_NODE) lane_work += (int64_t)t.w * 32 * nr32;
+    inf.node_lane_work = lane_work;
+    inf.device_bytes = (int64_t)P->arena_bytes;
+
+    *out = I.release();
+    return FFSAT_OK;
+}
+
+int ffsat_set_weights(ffsat_instance *I, const double *weights) {
+    t_err.clear();
+    if (!I || !weights) return fail(FFSAT_ERR_ARG, "NULL argument");
+    for (int32_t c = 0; c < I->m; ++c)
+        if (!(std::isfinite(weights[c]) && weights[c] >= 0.0)) return fail(FFSAT_ERR_WEIGHT, "constraint %d: bad weight", c);
+    I->w.assign(weights, weights + I->m);
+    fill_weights(I);
+    CUDA_TRY(cudaSetDevice(I->device));
+    unsigned char *base = I->d_arena;
+    for (int k = 0; k < 2; ++k) {
+        build_image(I, k);
+        CUDA_TRY(cudaMemcpy(base + I->off_image[k], I->image[k].data(), I->image[k].size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
+    CUDA_TRY(cudaMemcpy(base + I->off_clause_wd, I->clause_wd.data(), I->clause_wd.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(base + I->off_seg_wd, I->seg_wd.data(), I->seg_wd.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(base + I->off_cons_wd, I->cons_wd.data(), I->cons_wd.size() * sizeof(double), cudaMemcpyHostToDevice));
+    I->V32.f_const_d = I->V64.f_const_d = I->f_const;
+    I->V32.f_const_plain = I->V64.f_const_plain = I->f_const_plain;
+    for (DevView *W : {&I->V32, &I->V64}) {
+        W->fix_s1 = I->fix_s1;
+        W->fix_s2 = I->fix_s2;
+        W->fix_i1 = I->fix_i1;
+        W->fix_i12 = I->fix_i12;
+    }
+    I->V32.f_const_f = I->V64.f_const_f = (float)I->f_const;
+    return FFSAT_OK;
+}
+
+static int check_dtype(int32_t dtype) {
+    if (dtype != FFSAT_F32 && dtype != FFSAT_F64) return fail(FFSAT_ERR_ARG, "dtype must be FFSAT_F32 or FFSAT_F64");
+    return FFSAT_OK;
+}
+
+static inline int grid_for(int32_t B) { return B; }
+
+int ffsat_eval_grad(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, double *f, void *g, void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!I) return fail(FFSAT_ERR_ARG, "instance is NULL");
+    if (B < 0) return fail(FFSAT_ERR_ARG, "B must be >= 0");
+    int rc = check_dtype(dtype);
+    if (rc) return rc;
+    if (B == 0) return FFSAT_OK;
+    if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
+    CUDA_TRY(cudaSetDevice(I->device));
+    const bool f64 = dtype == FFSAT_F64;
+    FusedArgs a{};
+    a.B = B;
+    a.mode = MODE_EVAL;
+    a.x_in = x;
+    a.x_out = nullptr;
+    a.f = f;
+    a.g = g;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const DevView &V = f64 ? I->V64 : I->V32;
+    CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, f64 ? I->smem_mode64 : I->smem_mode32, a,
+                                                          f64 ? I->smem64 : I->smem32, grid_for(B), s, false));
+    t_launches = 1;
+    return FFSAT_OK;
+}
+
+int ffsat_eval_grad_plain64(ffsat_instance *I, int32_t B, const double *x, double *f, double *g, void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!I) return fail(FFSAT_ERR_ARG, "instance is NULL");
+    if (B < 0) return fail(FFSAT_ERR_ARG, "B must be >= 0");
+    if (B == 0) return FFSAT_OK;
+    if (!x || !f || !g) return fail(FFSAT_ERR_ARG, "x, f and g are required");
+    CUDA_TRY(cudaSetDevice(I->device));
+    int nl = 0;
+    CUDA_TRY(launch_plain64(I->V64, B, x, f, g, I->n_node_ids, I->d_node_ids, I->n_closed_ids, I->d_closed_ids,
+                            static_cast<cudaStream_t>(stream), &nl));
+    t_launches = nl;
+    return FFSAT_OK;
+}
+
+int ffsat_step(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat_step_args *args, uint8_t *solved,
+               int32_t *n_unsat, void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!I || !args) return fail(FFSAT_ERR_ARG, "NULL argument");
+    if (B < 0 || args->T < 0) return fail(FFSAT_ERR_ARG, "B and T must be >= 0");
+    if (!std::isfinite(args->lr)) return fail(FFSAT_ERR_ARG, "lr must be finite");
+    int rc = check_dtype(dtype);
+    if (rc) return rc;
+    if (B == 0) return FFSAT_OK;
+    if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
+    CUDA_TRY(cudaSetDevice(I->device));
+    const bool f64 = dtype == FFSAT_F64;
+    const int mode = f64 ? I->smem_mode64 : I->smem_mode32;
+    const size_t elem = f64 ? sizeof(double) : sizeof(float);
+    FusedArgs a{};
+    a.B = B;
+    a.mode = MODE_STEP;
+    a.x_in = x;
+    a.x_out = x;
+    a.solved = solved;
+    a.n_unsat = n_unsat;
+    a.sp.T = args->T;
+    a.sp.restart = args->restart;
+    a.sp.lr = args->lr;
+    a.sp.seed = args->seed;
+    a.sp.epoch = args->epoch;
+    a.sp.b_offset = args->b_offset;
+    if (mode != SMEM_FULL) {
+        const size_t need = (size_t)B * (size_t)I->n * elem;
+        if (need > I->scratch_bytes) {
+            if (I->d_scratch) CUDA_TRY(cudaFree(I->d_scratch));
+            I->d_scratch = nullptr;
+            I->scratch_bytes = 0;
+            CUDA_TRY(cudaMalloc(&I->d_scratch, need));
+            I->scratch_bytes = need;
+        }
+        a.g_scratch = I->d_scratch;
+    }
+    const DevView &V = f64 ? I->V64 : I->V32;
+    CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(B),
+                                                          static_cast<cudaStream_t>(stream), false));
+    t_launches = 1;
+    return FFSAT_OK;
+}
+
+int ffsat_check(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, uint8_t *sat, int32_t *n_unsat,
+                void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!I) return fail(FFSAT_ERR_ARG, "instance is NULL");
+    if (B < 0) return fail(FFSAT_ERR_ARG, "B must be >= 0");
+    int rc = check_dtype(dtype);
+    if (rc) return rc;
+    if (B == 0) return FFSAT_OK;
+    if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
+    CUDA_TRY(cudaSetDevice(I->device));
+    CUDA_TRY(launch_check(I->V32, dtype == FFSAT_F64, B, x, sat, n_unsat, static_cast<cudaStream_t>(stream)));
+    t_launches = 1;
+    return FFSAT_OK;
+}
+
+int ffsat_sync_status(ffsat_instance *I, void *stream) {
+    t_err.clear();
+    if (!I) return fail(FFSAT_ERR_ARG, "instance is NULL");
+    CUDA_TRY(cudaSetDevice(I->device));
+    CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int32_t st = 0;
+    CUDA_TRY(cudaMemcpy(&st, I->d_status, sizeof(st), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemset(I->d_status, 0, sizeof(int32_t)));
+    if (st & STATUS_NAN) return fail(FFSAT_ERR_NAN, "NaN found in x");
+    if (st) return fail(FFSAT_ERR_DEVICE, "device status 0x%x", st);
+    return FFSAT_OK;
+}
+
+int ffsat_instance_info(const ffsat_instance *I, ffsat_info *info) {
+    if (!I || !info) return fail(FFSAT_ERR_ARG, "NULL argument");
+    *info = I->info;
+    return FFSAT_OK;
+}
+
+void ffsat_free(ffsat_instance *I) {
+    if (!I) return;
+    cudaSetDevice(I->device);
+    if (I->d_arena) cudaFree(I->d_arena);
+    if (I->d_status) cudaFree(I->d_status);
+    if (I->d_scratch) cudaFree(I->d_scratch);
+    delete I;
+}
+
+}  // extern "C"

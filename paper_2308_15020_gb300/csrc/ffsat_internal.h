@@ -1,0 +1,129 @@
+// Internal data layout shared by the host code (ffsat_api.cpp) and the kernels.
+// Not part of the public C ABI.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace ffsat {
+
+// Literals per lane on the product (closed-form) path.
+constexpr int kProdR = 8;
+// Clauses per lane in one clause task.
+constexpr int kClausePerLane = 4;
+// Packed literal: (variable << 1) | negated.  Padding literal: -1.
+constexpr int32_t kPadLit = -1;
+
+// Warp tasks.  task.x = kind | (G << 8) where G = lanes per constraint segment
+// (power of two, 1..32); task.y = first item; task.z = item count; task.w = node
+// count J of the largest constraint in the task (node path only).
+enum : int32_t { TASK_CLAUSE = 0, TASK_PROD = 1, TASK_NODE = 2 };
+
+// Closed-form product constraints: FE = c0 + c1 prod_i (a + b y_i).
+enum : int32_t { PROD_OR = 0, PROD_XOR_EVEN = 1, PROD_XOR_ODD = 2 };
+
+// Where the fused kernel keeps a point's x and gradient accumulator, and the
+// instance's constraint data (SMEM_RES: all three in shared memory; in FP32 the
+// accumulator is then two int32 words per variable, see fix_s1).
+enum : int32_t { SMEM_FULL = 0, SMEM_X = 1, SMEM_NONE = 2, SMEM_RES = 3 };
+
+// Device status bits.
+enum : int32_t { STATUS_NAN = 1, STATUS_OTHER = 2 };
+
+// Everything a kernel reads, passed by value.
+struct DevView {
+    int32_t n;
+    int32_t m;
+    int32_t n_task;
+    int32_t n_seg;
+    const int4 *tasks;
+    // thread-per-clause path (clauses of <= 3 literals)
+    int32_t n_clause;
+    int32_t pad0;
+    const int4 *clauses;      // {l0, l1, l2, float bits of the FP32 weight}
+    const double *clause_wd;  // FP64 weights
+    // segment path (product and node constraints), sorted by length, descending:
+    // segmeta[s] = {offset into seg_lits, length, aux, float bits of the FP32 weight};
+    // aux = node-table offset (in nodes) on the node path, PROD_* kind on the product path
+    const int4 *segmeta;
+    const double *seg_wd;
+    const int32_t *seg_lits;  // packed literals
+    // Resident image {tasks | clauses | segmeta | seg_lits} (int4 units); tasks,
+    // clauses, segmeta and seg_lits above point into it.  When it fits in shared
+    // memory beside x and g, the kernel copies it there once per CTA.
+    const int4 *res_image;
+    int32_t res_int4, res_off_tasks, res_off_clauses, res_off_segmeta, res_off_lits, pad1;
+    // node tables, 8 reals per node: alpha.re, alpha.im, beta.re, beta.im, d.re, d.im, c.re, c.im
+    const float4 *tab_f;
+    const double *tab_d;
+    float pad_y_f;   // literal value that makes a node factor exactly 1 (+1 stable form, 0 paper form)
+    float f_const_f; // sum of w FE over constant constraints
+    double pad_y_d;
+    double f_const_d;
+    double f_const_plain;  // sum of w FE over constant constraints only (plain FP64 path)
+    // Two-word fixed-point gradient accumulator of the FP32 shared-resident mode:
+    // g = hi / 2^S1 + lo / 2^(S1+S2); fix_s1 = 2^S1, fix_s2 = 2^S2 and the inverses.
+    float fix_s1, fix_s2, fix_i1, fix_i12;
+    // exact-check CSR over all constraints (packed literals)
+    const int32_t *row_ptr;
+    const int32_t *lits;
+    const uint8_t *type;
+    const int32_t *param;
+    // plain FP64 comparator
+    const int32_t *cons_tab;  // node-table offset, or -1 for closed forms
+    const double *cons_wd;
+    int32_t *status;
+};
+
+struct StepParams {
+    int32_t T;
+    int32_t restart;
+    double lr;
+    uint64_t seed, epoch, b_offset;
+};
+
+// Threads per CTA of the fused kernel for (real type, node R).
+constexpr int fused_threads(bool f64, int node_r) {
+    return f64 ? (node_r >= 16 ? 128 : 256) : (node_r >= 16 ? 384 : (node_r > 0 ? 512 : 1024));
+}
+
+// Mode of the fused kernel.
+enum : int32_t { MODE_EVAL = 0, MODE_STEP = 1 };
+
+struct FusedArgs {
+    int32_t B;
+    int32_t mode;
+    const void *x_in;
+    void *x_out;
+    double *f;
+    void *g;          // eval: output rows (may be NULL)
+    void *g_scratch;  // step with g outside shared memory: [B, n] accumulator
+    StepParams sp;
+    uint8_t *solved;
+    int32_t *n_unsat;
+};
+
+// Fused-kernel launchers, one per (real type, node R); each handles the three
+// shared-memory modes.  With prepare_only the launcher only raises the kernel's
+// dynamic shared-memory limit to `smem`.
+#define FFSAT_FUSED_LAUNCHER(name)                                                                   \
+    cudaError_t name(const DevView &V, int smem_mode, const FusedArgs &a, size_t smem, int grid, \
+                     cudaStream_t s, bool prepare_only)
+FFSAT_FUSED_LAUNCHER(fused_f32_r0);
+FFSAT_FUSED_LAUNCHER(fused_f32_r8);
+FFSAT_FUSED_LAUNCHER(fused_f32_r16);
+FFSAT_FUSED_LAUNCHER(fused_f64_r0);
+FFSAT_FUSED_LAUNCHER(fused_f64_r8);
+FFSAT_FUSED_LAUNCHER(fused_f64_r16);
+
+// Exact checker: one CTA per point.
+cudaError_t launch_check(const DevView &V, bool f64, int B, const void *x, uint8_t *sat, int32_t *n_unsat,
+                         cudaStream_t s);
+// Plain FP64 comparator; *launches receives the number of kernels enqueued.
+cudaError_t launch_plain64(const DevView &V, int B, const double *x, double *f, double *g, int32_t n_node,
+                           const int32_t *node_ids, int32_t n_closed, const int32_t *closed_ids,
+                           cudaStream_t s, int *launches);
+
+}  // namespace ffsat

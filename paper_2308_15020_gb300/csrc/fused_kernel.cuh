@@ -1,0 +1,618 @@
+// Fused per-point kernel of the FastFourierSAT hot path.
+//
+// One CTA owns one restart point b (thread-level parallelism p_t of the paper's
+// "Acceleration with GPU" section maps to CTAs).  The point's x row and its
+// gradient accumulator live in shared memory when they fit, and so does the
+// instance's constraint data when it fits beside them; every constraint is
+// evaluated against them by warp tasks pulled from a shared-memory counter
+// (instruction-level parallelism p_i: constraints), and the literals of one
+// long constraint are spread over a segment of G lanes (data-level
+// parallelism p_d).
+//
+// Three constraint paths:
+//  * clause3: one thread per clause of <= 3 literals, FE = -1 + 2 q1 q2 q3 with
+//    q = (1+y)/2 and dFE/dy_i = prod_{l != i} q_l (footnote of App. B).
+//  * product: OR / XOR of any length <= 256, FE = c0 + c1 prod_i (a + b y_i)
+//    (App. B "Transform-Free", Cor. "Reduction"): an O(L) product with the
+//    all-but-one products formed by in-lane suffix/prefix products and a
+//    butterfly over the segment's lanes.
+//  * node: the DFT evaluation of Alg. 2 with conjugate symmetry.  For node j of
+//    N = L+1 roots of unity the factor of literal i is alpha_j + beta_j y_i
+//    (Eq. forward), the node value is the product over literals (Eq. reduction),
+//    FE = Re sum_j c_j prod_i(.) (Eq. inverse with the preprocessed
+//    coefficients) and dFE/dy_i = Re sum_j d_j prod_{l != i}(.) (Eq. chain),
+//    d_j = c_j beta_j.  The all-but-one products come from in-lane suffix
+//    products, a butterfly over the segment lanes and an in-lane prefix pass;
+//    NI nodes are processed per iteration to give the scheduler independent
+//    multiply chains.
+// Projected gradient descent (App. A.3 with a fixed step), the exact sign check
+// (Thm. "SAT Certificate", evaluated on integers) and the uniform restart of
+// Alg. 1 run in the same launch.
+//
+// Literals are packed as variable | (negated << 31).  Padding literals name two
+// dummy variables that follow the n real ones in shared memory: x[n] = +1 and
+// x[n+1] = 0, which make a clause, product or stable-form node factor (resp.
+// a paper-form node factor) exactly 1; their gradients land in dummy
+// accumulator slots.  When x or g live in global memory, accesses to the dummy
+// variables are resolved without touching memory.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "ffsat_internal.h"
+
+namespace ffsat {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr uint32_t kVarMask = 0x7fffffffu;
+constexpr uint32_t kSignBit = 0x80000000u;
+
+template <typename R>
+struct C2 {
+    R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ C2<R> cmul(C2<R> a, C2<R> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+template <typename R>
+struct Node {
+    C2<R> a, b, d, c;
+};
+
+__device__ __forceinline__ Node<float> load_node(const DevView &V, float, int idx) {
+    const float4 p = __ldg(&V.tab_f[2 * idx]);
+    const float4 q = __ldg(&V.tab_f[2 * idx + 1]);
+    return {{p.x, p.y}, {p.z, p.w}, {q.x, q.y}, {q.z, q.w}};
+}
+
+__device__ __forceinline__ Node<double> load_node(const DevView &V, double, int idx) {
+    const double2 *t = reinterpret_cast<const double2 *>(V.tab_d) + 4 * idx;
+    const double2 p = __ldg(t), q = __ldg(t + 1), r = __ldg(t + 2), s = __ldg(t + 3);
+    return {{p.x, p.y}, {q.x, q.y}, {r.x, r.y}, {s.x, s.y}};
+}
+
+// Where the warp tasks read the constraint data from: global memory, or the
+// CTA's shared-memory copy of the resident image.
+struct Src {
+    const int4 *tasks;
+    const int4 *clauses;
+    const int4 *segmeta;
+    const int32_t *seg_lits;
+};
+
+template <typename R>
+__device__ __forceinline__ R seg_weight(const DevView &V, int4 meta, int c);
+template <>
+__device__ __forceinline__ float seg_weight<float>(const DevView &, int4 meta, int) { return __int_as_float(meta.w); }
+template <>
+__device__ __forceinline__ double seg_weight<double>(const DevView &V, int4, int c) { return __ldg(&V.seg_wd[c]); }
+
+template <typename R>
+__device__ __forceinline__ R clause_weight(const DevView &V, int4 cl, int idx);
+template <>
+__device__ __forceinline__ float clause_weight<float>(const DevView &, int4 cl, int) { return __int_as_float(cl.w); }
+template <>
+__device__ __forceinline__ double clause_weight<double>(const DevView &V, int4, int idx) {
+    return __ldg(&V.clause_wd[idx]);
+}
+
+// Multiply by -1 when the sign bit of the packed literal is set.
+__device__ __forceinline__ float flip(float x, uint32_t lp) {
+    return __int_as_float(__float_as_int(x) ^ (int)(lp & kSignBit));
+}
+__device__ __forceinline__ double flip(double x, uint32_t lp) {
+    return __longlong_as_double(__double_as_longlong(x) ^ ((long long)(lp & kSignBit) << 32));
+}
+
+// y = sigma x[v].  XG: where x lives (dummy variables n, n+1 exist in shared memory).
+template <typename R, int XG>
+__device__ __forceinline__ R gather(const R *xrow, uint32_t lp, int n) {
+    const uint32_t v = lp & kVarMask;
+    R xv;
+    if constexpr (XG == SMEM_NONE)
+        xv = v < (uint32_t)n ? xrow[v] : (v == (uint32_t)n ? R(1) : R(0));
+    else
+        xv = xrow[v];
+    return flip(xv, lp);
+}
+
+// Gradient accumulators.  Plain: one real per variable updated with atomicAdd
+// (shared or global memory).  Fixed: two int32 words per variable in shared
+// memory updated with the native integer reduction; a contribution c is split
+// into hi = round(c 2^S1) and lo = round((c 2^S1 - hi) 2^S2), both rounded by
+// adding 1.5 * 2^23 (exact round-to-nearest for |t| < 2^22, which the host's
+// choice of S1, S2 guarantees).  Padding literals (dummy variables) are
+// skipped: many lanes of a warp share the dummy and same-address updates
+// serialise.
+template <typename R>
+struct PlainAcc {
+    R *g;
+    __device__ __forceinline__ void add(uint32_t v, R c) const { atomicAdd(&g[v], c); }
+    __device__ __forceinline__ void addf(uint32_t v, R c) const { atomicAdd(&g[v], c); }
+    __device__ __forceinline__ R get(int v) const { return g[v]; }
+    __device__ __forceinline__ void zero(int v) const { g[v] = R(0); }
+};
+
+// Clause and node contributions (bounded by their weight) go to the fixed-point
+// words; product contributions (XOR and long clauses, whose gradients are
+// products of many factors and can be far below the fixed-point resolution)
+// go to an FP32 word updated with atomicAdd.
+struct FixAcc {
+    int *hi;
+    int *lo;
+    float *gf;
+    float s1, s2, i1, i12;
+    __device__ __forceinline__ void add(uint32_t v, float c) const {
+        constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
+        const float m1 = __fmaf_rn(c, s1, kMagic);  // c 2^S1 is exact; one rounding to an integer
+        const int h = __float_as_int(m1) - 0x4B400000;
+        const float r = __fmaf_rn(c, s1, __fsub_rn(kMagic, m1));  // exact residual in [-1/2, 1/2]
+        const float m2 = __fmaf_rn(r, s2, kMagic);
+        const int l = __float_as_int(m2) - 0x4B400000;
+        const unsigned a = (unsigned)__cvta_generic_to_shared(hi + v);
+        const unsigned b = (unsigned)__cvta_generic_to_shared(lo + v);
+        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(h) : "memory");
+        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(b), "r"(l) : "memory");
+    }
+    __device__ __forceinline__ void addf(uint32_t v, float c) const { atomicAdd(&gf[v], c); }
+    __device__ __forceinline__ float get(int v) const {
+        return __fmaf_rn((float)lo[v], i12, __fmaf_rn((float)hi[v], i1, gf[v]));
+    }
+    __device__ __forceinline__ void zero(int v) const {
+        hi[v] = 0;
+        lo[v] = 0;
+        gf[v] = 0.0f;
+    }
+};
+
+template <typename R, typename Acc>
+__device__ __forceinline__ void scatter(const Acc &acc, uint32_t lp, R val, int n) {
+    const uint32_t v = lp & kVarMask;
+    if (v < (uint32_t)n) acc.add(v, flip(val, lp));
+}
+
+template <typename R, typename Acc>
+__device__ __forceinline__ void scatter_f(const Acc &acc, uint32_t lp, R val, int n) {
+    const uint32_t v = lp & kVarMask;
+    if (v < (uint32_t)n) acc.addf(v, flip(val, lp));
+}
+
+// R consecutive packed literals of this lane (R a multiple of 4, 16-byte aligned).
+template <int RL>
+__device__ __forceinline__ void load_lits(const int32_t *p, uint32_t (&lp)[RL]) {
+    const int4 *q = reinterpret_cast<const int4 *>(p);
+#pragma unroll
+    for (int k = 0; k < RL / 4; ++k) {
+        const int4 t = q[k];
+        lp[4 * k + 0] = (uint32_t)t.x;
+        lp[4 * k + 1] = (uint32_t)t.y;
+        lp[4 * k + 2] = (uint32_t)t.z;
+        lp[4 * k + 3] = (uint32_t)t.w;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// clause3 path: 32 * kClausePerLane clauses per task (the list is padded)
+// ---------------------------------------------------------------------------
+// FE = 2 w q0 q1 q2 - w; the constant -w is folded into f_const on the host,
+// so facc collects 2 w q0 q1 q2 only.
+template <typename R, int XG, typename Acc>
+__device__ __forceinline__ void clause_task(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
+                                            const Acc &acc, bool want_g, R &facc) {
+    const int n = V.n;
+    int4 cl[kClausePerLane];
+#pragma unroll
+    for (int k = 0; k < kClausePerLane; ++k) cl[k] = S.clauses[task.y + k * 32 + lane];
+#pragma unroll
+    for (int k = 0; k < kClausePerLane; ++k) {
+        const R w = clause_weight<R>(V, cl[k], task.y + k * 32 + lane);
+        const R y0 = gather<R, XG>(xrow, (uint32_t)cl[k].x, n);
+        const R y1 = gather<R, XG>(xrow, (uint32_t)cl[k].y, n);
+        const R y2 = gather<R, XG>(xrow, (uint32_t)cl[k].z, n);
+        const R q0 = R(0.5) + R(0.5) * y0;
+        const R q1 = R(0.5) + R(0.5) * y1;
+        const R q2 = R(0.5) + R(0.5) * y2;
+        const R wq12 = w * (q1 * q2);
+        facc += wq12 * (R(1) + y0);  // 2 w q0 q1 q2
+        if (want_g) {
+            const R wq0 = w * q0;
+            scatter<R>(acc, (uint32_t)cl[k].x, wq12, n);
+            scatter<R>(acc, (uint32_t)cl[k].y, wq0 * q2, n);
+            scatter<R>(acc, (uint32_t)cl[k].z, wq0 * q1, n);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// product path (closed forms), kProdR literals per lane, G lanes per constraint
+// ---------------------------------------------------------------------------
+template <typename R, int XG, typename Acc>
+__device__ __forceinline__ void prod_task(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
+                                          const Acc &acc, bool want_g, R &facc) {
+    constexpr int RL = kProdR;
+    const int n = V.n;
+    const int G = task.x >> 8;
+    const int seg = lane >> (__ffs(G) - 1);
+    const int sl = lane & (G - 1);
+    const int c = task.y + seg;
+    const bool valid = seg < task.z;
+    uint32_t lp[RL];
+    int kind = PROD_OR;
+    R w = R(0);
+    if (valid) {
+        const int4 meta = S.segmeta[c];
+        kind = meta.z;
+        w = seg_weight<R>(V, meta, c);
+        load_lits<RL>(S.seg_lits + meta.x + sl * RL, lp);
+    } else {
+#pragma unroll
+        for (int r = 0; r < RL; ++r) lp[r] = (uint32_t)n;
+    }
+    const R a = kind == PROD_OR ? R(0.5) : R(0);
+    const R bco = kind == PROD_OR ? R(0.5) : R(1);
+    const R c0 = kind == PROD_OR ? R(-1) : R(0);
+    const R c1 = kind == PROD_OR ? R(2) : (kind == PROD_XOR_ODD ? R(1) : R(-1));
+    R u[RL];
+#pragma unroll
+    for (int r = 0; r < RL; ++r) u[r] = a + bco * gather<R, XG>(xrow, lp[r], n);  // padding: y = +1, u = 1
+    R suf[RL];
+    suf[RL - 1] = R(1);
+#pragma unroll
+    for (int r = RL - 1; r >= 1; --r) suf[r - 1] = suf[r] * u[r];
+    R P = u[0] * suf[0];
+    R X = R(1);
+    for (int s = 1; s < G; s <<= 1) {
+        const R Pp = __shfl_xor_sync(kFull, P, s);
+        X *= Pp;
+        P *= Pp;
+    }
+    if (sl == 0) facc += w * (c0 + c1 * P);
+    if (want_g) {
+        R pre = w * c1 * bco * X;
+#pragma unroll
+        for (int r = 0; r < RL; ++r) {
+            scatter_f<R>(acc, lp[r], pre * suf[r], n);
+            pre *= u[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// node path (DFT evaluation), NR literals per lane, G lanes per constraint,
+// NI nodes per iteration
+// ---------------------------------------------------------------------------
+template <typename R, int NR, int NI, int XG, typename Acc>
+__device__ __forceinline__ void node_task(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
+                                          const Acc &acc, bool want_g, R &facc) {
+    const int n = V.n;
+    const int G = task.x >> 8;
+    const int seg = lane >> (__ffs(G) - 1);
+    const int sl = lane & (G - 1);
+    const int c = task.y + seg;
+    const bool valid = seg < task.z;
+    int L = 0, toff = 0;
+    const int32_t *lits = nullptr;
+    R w = R(0);
+    R y[NR];
+    if (valid) {
+        const int4 meta = S.segmeta[c];
+        L = meta.y;
+        toff = meta.z;
+        w = seg_weight<R>(V, meta, c);
+        lits = S.seg_lits + meta.x + sl * NR;
+        uint32_t lp[NR];
+        load_lits<NR>(lits, lp);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) y[r] = gather<R, XG>(xrow, lp[r], n);
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) y[r] = R(0);
+    }
+    const int Jc = valid ? (L + 1) / 2 + 1 : 0;  // nodes j = 0 .. floor(N/2), N = L + 1
+    R gacc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) gacc[r] = R(0);
+    R fe = R(0);
+    const int J = task.w;
+    const Node<R> zero = {{R(0), R(0)}, {R(0), R(0)}, {R(0), R(0)}, {R(0), R(0)}};
+    Node<R> nd[NI];
+#pragma unroll
+    for (int q = 0; q < NI; ++q) nd[q] = q < Jc ? load_node(V, R(0), toff + q) : zero;
+    for (int j0 = 0; j0 < J; j0 += NI) {
+        Node<R> nx[NI];
+#pragma unroll
+        for (int q = 0; q < NI; ++q) nx[q] = (j0 + NI + q < Jc) ? load_node(V, R(0), toff + j0 + NI + q) : zero;
+        // in-lane suffix products suf[r] = prod_{k > r} f_k
+        C2<R> suf[NI][NR];
+#pragma unroll
+        for (int q = 0; q < NI; ++q) suf[q][NR - 1] = {R(1), R(0)};
+#pragma unroll
+        for (int r = NR - 1; r >= 1; --r) {
+#pragma unroll
+            for (int q = 0; q < NI; ++q) {
+                const C2<R> f = {nd[q].a.re + nd[q].b.re * y[r], nd[q].a.im + nd[q].b.im * y[r]};
+                suf[q][r - 1] = cmul(suf[q][r], f);
+            }
+        }
+        C2<R> P[NI], X[NI];
+#pragma unroll
+        for (int q = 0; q < NI; ++q) {
+            const C2<R> f0 = {nd[q].a.re + nd[q].b.re * y[0], nd[q].a.im + nd[q].b.im * y[0]};
+            P[q] = cmul(f0, suf[q][0]);  // this lane's product
+            X[q] = {R(1), R(0)};         // product of the other lanes of the segment
+        }
+        for (int s = 1; s < G; s <<= 1) {
+#pragma unroll
+            for (int q = 0; q < NI; ++q) {
+                const C2<R> Pp = {__shfl_xor_sync(kFull, P[q].re, s), __shfl_xor_sync(kFull, P[q].im, s)};
+                X[q] = cmul(X[q], Pp);
+                P[q] = cmul(P[q], Pp);
+            }
+        }
+        C2<R> pre[NI];
+#pragma unroll
+        for (int q = 0; q < NI; ++q) {
+            fe += nd[q].c.re * P[q].re - nd[q].c.im * P[q].im;  // Re(c_j Q_j)
+            pre[q] = cmul(nd[q].d, X[q]);                      // d_j prod(other lanes)
+        }
+        // prefix pass: pre = d_j X prod_{k < r} f_k
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+#pragma unroll
+            for (int q = 0; q < NI; ++q) {
+                gacc[r] += pre[q].re * suf[q][r].re - pre[q].im * suf[q][r].im;
+                if (r + 1 < NR) {
+                    const C2<R> f = {nd[q].a.re + nd[q].b.re * y[r], nd[q].a.im + nd[q].b.im * y[r]};
+                    pre[q] = cmul(pre[q], f);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NI; ++q) nd[q] = nx[q];
+    }
+    if (valid && sl == 0) facc += w * fe;
+    if (want_g && valid) {
+        uint32_t lp[NR];
+        load_lits<NR>(lits, lp);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) scatter<R>(acc, lp[r], w * gacc[r], n);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// block helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+__device__ __forceinline__ int warp_sum(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+    return v;
+}
+
+// Sum over the block; the result is valid in thread 0.  Contains __syncthreads.
+template <typename T>
+__device__ __forceinline__ T block_sum(T v, T *red) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    T t = T(0);
+    if (wid == 0) {
+        t = lane < nw ? red[lane] : T(0);
+        t = warp_sum(t);
+    }
+    return t;
+}
+
+// Exact check of sgn(xrow): number of violated constraints (valid in thread 0).
+template <typename R>
+__device__ __forceinline__ int block_unsat(const DevView &V, const R *xrow, int *ired) {
+    int cnt = 0;
+    for (int c = threadIdx.x; c < V.m; c += blockDim.x) {
+        const int a = __ldg(&V.row_ptr[c]), e = __ldg(&V.row_ptr[c + 1]);
+        int s = 0;
+        for (int i = a; i < e; ++i) {
+            const uint32_t lp = (uint32_t)__ldg(&V.lits[i]);
+            const int var_true = xrow[lp & kVarMask] < R(0);  // sgn(x) = -1 encodes True
+            s += var_true ^ (int)(lp >> 31);
+        }
+        const int t = __ldg(&V.type[c]), p = __ldg(&V.param[c]);
+        const bool ok = t == 0 ? s >= 1 : (t == 1 ? ((s & 1) == (p & 1)) : s >= p);
+        cnt += ok ? 0 : 1;
+    }
+    return block_sum(cnt, ired);
+}
+
+__device__ __forceinline__ uint64_t splitmix64(uint64_t state) {
+    uint64_t z = state + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Uniform restart value on the 24-bit grid of [-1, 1).
+template <typename R>
+__device__ __forceinline__ R restart_value(uint64_t key_b, uint64_t v) {
+    const uint64_t h = splitmix64(key_b ^ v);
+    const int u = (int)(h >> 40) - (1 << 23);
+    return R(u) * R(1.0 / 8388608.0);
+}
+
+// ---------------------------------------------------------------------------
+// the fused kernel
+// ---------------------------------------------------------------------------
+template <typename R, int NR, int NI, int SM, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) fused_kernel(const DevView V, const FusedArgs A) {
+    // SMEM_RES keeps x and g in shared memory like SMEM_FULL and adds the resident image.
+    constexpr bool RES = SM == SMEM_RES;
+    constexpr int XG = RES ? SMEM_FULL : SM;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_ctr;
+    __shared__ double s_red[32];
+    __shared__ int s_ired[32];
+
+    const int n = V.n;
+    const int npad = (n + 2 + 3) & ~3;  // n variables + 2 dummies, rounded to 4
+    const int tid = threadIdx.x, lane = tid & 31;
+    R *xs = reinterpret_cast<R *>(smem_raw);
+    R *gs = xs + npad;
+    const bool step = A.mode == MODE_STEP;
+    const R *x_in = static_cast<const R *>(A.x_in);
+    R *x_out = static_cast<R *>(A.x_out);
+    R *g_out = static_cast<R *>(A.g);
+    R *g_scr = static_cast<R *>(A.g_scratch);
+    const R lr = R(A.sp.lr);
+
+    // FP32 shared-resident mode: x | g hi words | g lo words | g FP32 words | image;
+    // otherwise x | g | image.
+    constexpr bool FIX = RES && sizeof(R) == 4;
+    using Acc = typename std::conditional<FIX, FixAcc, PlainAcc<R>>::type;
+    const size_t img_off = FIX ? 4 * (size_t)npad * 4 : 2 * (size_t)npad * sizeof(R);
+
+    Src S;
+    if constexpr (RES) {
+        int4 *img = reinterpret_cast<int4 *>(smem_raw + img_off);
+        for (int i = tid; i < V.res_int4; i += THREADS) img[i] = __ldg(&V.res_image[i]);
+        S.tasks = img + V.res_off_tasks;
+        S.clauses = img + V.res_off_clauses;
+        S.segmeta = img + V.res_off_segmeta;
+        S.seg_lits = reinterpret_cast<const int32_t *>(img + V.res_off_lits);
+    } else {
+        S.tasks = V.tasks;
+        S.clauses = V.clauses;
+        S.segmeta = V.segmeta;
+        S.seg_lits = V.seg_lits;
+    }
+
+    for (int b = blockIdx.x; b < A.B; b += gridDim.x) {
+        const size_t rowoff = (size_t)b * (size_t)n;
+        // ---- stage x ----
+        const R *xrow;
+        if constexpr (XG != SMEM_NONE) {
+            bool bad = false;
+            for (int v = tid; v < n; v += THREADS) {
+                const R xv = x_in[rowoff + v];
+                bad |= isnan(xv);
+                xs[v] = xv;
+            }
+            if (tid == 0) {
+                xs[n] = R(1);
+                xs[n + 1] = R(0);
+            }
+            if (bad) atomicOr(V.status, STATUS_NAN);
+            xrow = xs;
+        } else {
+            if (step && x_out != x_in) {
+                for (int v = tid; v < n; v += THREADS) x_out[rowoff + v] = x_in[rowoff + v];
+                __syncthreads();
+            }
+            xrow = step ? x_out + rowoff : x_in + rowoff;
+            bool bad = false;
+            for (int v = tid; v < n; v += THREADS) bad |= isnan(xrow[v]);
+            if (bad) atomicOr(V.status, STATUS_NAN);
+        }
+        Acc G;
+        bool want_g;
+        int glen;
+        if constexpr (FIX) {
+            G.hi = reinterpret_cast<int *>(smem_raw + (size_t)npad * 4);
+            G.lo = G.hi + npad;
+            G.gf = reinterpret_cast<float *>(G.lo + npad);
+            G.s1 = V.fix_s1;
+            G.s2 = V.fix_s2;
+            G.i1 = V.fix_i1;
+            G.i12 = V.fix_i12;
+            want_g = step || g_out != nullptr;
+            glen = npad;
+        } else if constexpr (XG == SMEM_FULL) {
+            G.g = gs;
+            want_g = step || g_out != nullptr;
+            glen = npad;
+        } else {
+            G.g = step ? g_scr + rowoff : (g_out ? g_out + rowoff : nullptr);
+            want_g = G.g != nullptr;
+            glen = n;
+        }
+        if (want_g)
+            for (int v = tid; v < glen; v += THREADS) G.zero(v);
+
+        const int iters = step ? A.sp.T : 1;
+        for (int it = 0; it < iters; ++it) {
+            if (tid == 0) s_ctr = 0;
+            __syncthreads();
+            R facc = R(0);
+            for (;;) {
+                int t = 0;
+                if (lane == 0) t = atomicAdd(&s_ctr, 1);
+                t = __shfl_sync(kFull, t, 0);
+                if (t >= V.n_task) break;
+                const int4 task = S.tasks[t];
+                const int kind = task.x & 0xff;
+                if (kind == TASK_CLAUSE) {
+                    clause_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
+                } else if (kind == TASK_PROD) {
+                    prod_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
+                } else {
+                    if constexpr (NR > 0) node_task<R, NR, NI, XG>(V, S, task, lane, xrow, G, want_g, facc);
+                }
+            }
+            __syncthreads();
+            if (!step) {
+                if (A.f) {
+                    const double tot = block_sum((double)facc, s_red);
+                    if (tid == 0) A.f[b] = tot + V.f_const_d;
+                }
+                if constexpr (XG == SMEM_FULL) {
+                    if (g_out)
+                        for (int v = tid; v < n; v += THREADS) g_out[rowoff + v] = G.get(v);
+                }
+            } else {
+                // projected gradient step x <- clip(x - lr g, -1, 1); reset the accumulator
+                R *xw = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
+                for (int v = tid; v < n; v += THREADS) {
+                    R z = xw[v] - lr * G.get(v);
+                    z = z < R(-1) ? R(-1) : (z > R(1) ? R(1) : z);
+                    xw[v] = z;
+                    G.zero(v);
+                }
+                __syncthreads();
+            }
+        }
+        if (step) {
+            const R *xc = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
+            const int unsat = block_unsat<R>(V, xc, s_ired);
+            if (tid == 0) s_ired[0] = unsat;
+            __syncthreads();
+            const int u = s_ired[0];
+            if (tid == 0) {
+                if (A.solved) A.solved[b] = (uint8_t)(u == 0);
+                if (A.n_unsat) A.n_unsat[b] = u;
+            }
+            R *xw = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
+            if (u != 0 && A.sp.restart) {
+                const uint64_t kb =
+                    splitmix64(splitmix64(splitmix64(A.sp.seed) ^ A.sp.epoch) ^ (A.sp.b_offset + (uint64_t)b));
+                for (int v = tid; v < n; v += THREADS) xw[v] = restart_value<R>(kb, (uint64_t)v);
+            }
+            if constexpr (XG != SMEM_NONE) {
+                for (int v = tid; v < n; v += THREADS) x_out[rowoff + v] = xs[v];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace dev
+}  // namespace ffsat

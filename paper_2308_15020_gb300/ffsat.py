@@ -1,0 +1,271 @@
+"""Python binding of libffsat.so (the CUDA C-ABI library).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  PyTorch tensors supply device memory and streams.  The module
+fails loudly when the compiled library is missing; there is no CPU fallback.
+
+The C entry points are reachable under their own names through ``lib()``
+(``lib().ffsat_eval_grad(...)``); the ``Instance`` class wraps them for torch
+tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "lib", "libffsat.so")
+
+FFSAT_OR, FFSAT_XOR, FFSAT_ATLEAST = 0, 1, 2
+FFSAT_F32, FFSAT_F64 = 0, 1
+FFSAT_FORM_STABLE, FFSAT_FORM_PAPER = 0, 1
+FFSAT_MAX_LEN = 512
+
+ERRORS = {
+    0: "FFSAT_OK",
+    -1: "FFSAT_ERR_ARG",
+    -2: "FFSAT_ERR_VAR_RANGE",
+    -3: "FFSAT_ERR_DUPVAR",
+    -4: "FFSAT_ERR_EMPTY",
+    -5: "FFSAT_ERR_PARAM",
+    -6: "FFSAT_ERR_WEIGHT",
+    -7: "FFSAT_ERR_TOOLONG",
+    -8: "FFSAT_ERR_CUDA",
+    -9: "FFSAT_ERR_NAN",
+    -10: "FFSAT_ERR_DEVICE",
+}
+
+# Every symbol include/ffsat.h declares.
+SYMBOLS = (
+    "ffsat_default_options",
+    "ffsat_load_instance",
+    "ffsat_set_weights",
+    "ffsat_eval_grad",
+    "ffsat_eval_grad_plain64",
+    "ffsat_step",
+    "ffsat_check",
+    "ffsat_sync_status",
+    "ffsat_instance_info",
+    "ffsat_last_launch_count",
+    "ffsat_last_error",
+    "ffsat_free",
+)
+
+
+class FFSatError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("form", C.c_int32), ("node_all", C.c_int32), ("node_r", C.c_int32), ("autotune", C.c_int32),
+                ("device", C.c_int32)]
+
+
+class StepArgs(C.Structure):
+    _fields_ = [("T", C.c_int32), ("restart", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64),
+                ("epoch", C.c_uint64), ("b_offset", C.c_uint64)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nnz", C.c_int64), ("n_clause3", C.c_int32),
+                ("n_product", C.c_int32), ("n_node", C.c_int32), ("n_const", C.c_int32), ("n_tables", C.c_int32),
+                ("n_tasks", C.c_int32), ("node_r", C.c_int32), ("smem_mode_f32", C.c_int32),
+                ("smem_mode_f64", C.c_int32), ("threads_f32", C.c_int32), ("node_lane_work", C.c_int64),
+                ("device_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+_vp = C.c_void_p
+
+
+def lib():
+    """Load libffsat.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise FileNotFoundError(
+                f"{LIB_PATH} is missing: build it with `python -c 'import __graft_entry__ as g; g.build()'` "
+                "or `python paper_2308_15020_gb300/build.py`")
+        L = C.CDLL(LIB_PATH)
+        L.ffsat_default_options.argtypes = [C.POINTER(Options)]
+        L.ffsat_default_options.restype = None
+        L.ffsat_load_instance.argtypes = [C.c_int32, C.c_int32, _vp, _vp, _vp, _vp, _vp, C.POINTER(Options),
+                                          C.POINTER(_vp)]
+        L.ffsat_load_instance.restype = C.c_int
+        L.ffsat_set_weights.argtypes = [_vp, _vp]
+        L.ffsat_set_weights.restype = C.c_int
+        L.ffsat_eval_grad.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
+        L.ffsat_eval_grad.restype = C.c_int
+        L.ffsat_eval_grad_plain64.argtypes = [_vp, C.c_int32, _vp, _vp, _vp, _vp]
+        L.ffsat_eval_grad_plain64.restype = C.c_int
+        L.ffsat_step.argtypes = [_vp, C.c_int32, _vp, C.c_int32, C.POINTER(StepArgs), _vp, _vp, _vp]
+        L.ffsat_step.restype = C.c_int
+        L.ffsat_check.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
+        L.ffsat_check.restype = C.c_int
+        L.ffsat_sync_status.argtypes = [_vp, _vp]
+        L.ffsat_sync_status.restype = C.c_int
+        L.ffsat_instance_info.argtypes = [_vp, C.POINTER(Info)]
+        L.ffsat_instance_info.restype = C.c_int
+        L.ffsat_last_launch_count.argtypes = []
+        L.ffsat_last_launch_count.restype = C.c_int32
+        L.ffsat_last_error.argtypes = []
+        L.ffsat_last_error.restype = C.c_char_p
+        L.ffsat_free.argtypes = [_vp]
+        L.ffsat_free.restype = None
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise FFSatError(rc, lib().ffsat_last_error().decode())
+
+
+def last_launch_count() -> int:
+    return int(lib().ffsat_last_launch_count())
+
+
+def _ptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _dtype_code(t) -> int:
+    import torch
+
+    if t.dtype == torch.float32:
+        return FFSAT_F32
+    if t.dtype == torch.float64:
+        return FFSAT_F64
+    raise TypeError(f"x must be float32 or float64, got {t.dtype}")
+
+
+def _need_cuda_contig(t, name):
+    if not (t.is_cuda and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+
+
+class Instance:
+    """An instance loaded into the library (``ffsat_load_instance``)."""
+
+    def __init__(self, inst, form: int = FFSAT_FORM_STABLE, node_all: bool = False, node_r: int = 0,
+                 autotune: bool = False, device: int = -1):
+        import numpy as np
+
+        self.n = int(inst.n)
+        self.m = int(inst.ctype.shape[0])
+        self._rp = np.ascontiguousarray(inst.row_ptr, dtype=np.int64)
+        self._lits = np.ascontiguousarray(inst.lits, dtype=np.int32)
+        self._ty = np.ascontiguousarray(inst.ctype, dtype=np.uint8)
+        self._pa = np.ascontiguousarray(inst.param, dtype=np.int32)
+        self._w = np.ascontiguousarray(inst.weights, dtype=np.float64)
+        opt = Options()
+        lib().ffsat_default_options(C.byref(opt))
+        opt.form, opt.node_all, opt.node_r, opt.autotune, opt.device = form, int(node_all), node_r, int(autotune), device
+        h = _vp()
+        rc = lib().ffsat_load_instance(self.n, self.m, self._rp.ctypes.data, self._lits.ctypes.data,
+                                       self._ty.ctypes.data, self._pa.ctypes.data, self._w.ctypes.data,
+                                       C.byref(opt), C.byref(h))
+        _check(rc)
+        self.handle = h.value
+
+    # -- lifetime --------------------------------------------------------------------------
+    def free(self):
+        if getattr(self, "handle", None):
+            lib().ffsat_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(lib().ffsat_instance_info(self.handle, C.byref(inf)))
+        return inf.as_dict()
+
+    def set_weights(self, w):
+        import numpy as np
+
+        w = np.ascontiguousarray(w, dtype=np.float64)
+        if w.shape != (self.m,):
+            raise ValueError("weights must have shape (m,)")
+        _check(lib().ffsat_set_weights(self.handle, w.ctypes.data))
+
+    # -- hot path ----------------------------------------------------------------------------
+    def eval_grad(self, x, f=None, g=None, want_f: bool = True, want_g: bool = True, stream=None):
+        """f[b] = F(x_b) (float64) and g = grad F (dtype of x)."""
+        import torch
+
+        _need_cuda_contig(x, "x")
+        B = x.shape[0]
+        if want_f and f is None:
+            f = torch.empty(B, dtype=torch.float64, device=x.device)
+        if want_g and g is None:
+            g = torch.empty_like(x)
+        rc = lib().ffsat_eval_grad(self.handle, B, x.data_ptr(), _dtype_code(x), _ptr(f if want_f else None),
+                                   _ptr(g if want_g else None), _stream(stream))
+        _check(rc)
+        return f, g
+
+    def eval_grad_plain64(self, x, f=None, g=None, stream=None):
+        import torch
+
+        _need_cuda_contig(x, "x")
+        if x.dtype != torch.float64:
+            raise TypeError("the plain FP64 path takes float64 x")
+        B = x.shape[0]
+        f = torch.empty(B, dtype=torch.float64, device=x.device) if f is None else f
+        g = torch.empty_like(x) if g is None else g
+        _check(lib().ffsat_eval_grad_plain64(self.handle, B, x.data_ptr(), f.data_ptr(), g.data_ptr(),
+                                             _stream(stream)))
+        return f, g
+
+    def step(self, x, T: int, lr: float, seed: int = 0, epoch: int = 0, b_offset: int = 0, restart: bool = True,
+             solved=None, n_unsat=None, stream=None):
+        """One round of fixed-step projected GD + exact check + restart, in place on x."""
+        import torch
+
+        _need_cuda_contig(x, "x")
+        B = x.shape[0]
+        if solved is None:
+            solved = torch.empty(B, dtype=torch.uint8, device=x.device)
+        if n_unsat is None:
+            n_unsat = torch.empty(B, dtype=torch.int32, device=x.device)
+        a = StepArgs(int(T), int(restart), float(lr), int(seed) & (2**64 - 1), int(epoch), int(b_offset))
+        _check(lib().ffsat_step(self.handle, B, x.data_ptr(), _dtype_code(x), C.byref(a), solved.data_ptr(),
+                                n_unsat.data_ptr(), _stream(stream)))
+        return solved, n_unsat
+
+    def check(self, x, sat=None, n_unsat=None, stream=None):
+        import torch
+
+        _need_cuda_contig(x, "x")
+        B = x.shape[0]
+        sat = torch.empty(B, dtype=torch.uint8, device=x.device) if sat is None else sat
+        n_unsat = torch.empty(B, dtype=torch.int32, device=x.device) if n_unsat is None else n_unsat
+        _check(lib().ffsat_check(self.handle, B, x.data_ptr(), _dtype_code(x), sat.data_ptr(), n_unsat.data_ptr(),
+                                 _stream(stream)))
+        return sat, n_unsat
+
+    def sync_status(self, stream=None):
+        _check(lib().ffsat_sync_status(self.handle, _stream(stream)))
+
+
+def load_instance(inst, **kw) -> Instance:
+    return Instance(inst, **kw)

@@ -1,0 +1,309 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle.
+
+Inputs are seeded and synthetic.  Small cases span several warp tasks and
+ragged tails of every path; full-size cases use the launch configuration the
+benchmark times and compare on sampled points."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2308_15020_gb300 import gen
+from parity import compare, mixed_instance, to_np
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _dev():
+    from paper_2308_15020_gb300 import ffsat
+
+    return ffsat
+
+
+def _x(arr, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(arr)).to(device="cuda", dtype=dtype).contiguous()
+
+
+@pytest.fixture(scope="module")
+def F():
+    return _dev()
+
+
+# ---------------------------------------------------------------------------------------------
+# eval_grad: mixed constraint types, all paths, FP32 and FP64
+# ---------------------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("dist", ["uniform", "near_corner", "corner"])
+def test_mixed_fp32(F, dist):
+    inst = mixed_instance(1)
+    B = 37
+    x = {"uniform": gen.uniform_points, "near_corner": gen.near_corner_points, "corner": gen.corner_points}[dist](
+        B, inst.n, 3)
+    h = F.Instance(inst)
+    info = h.info()
+    assert info["n_clause3"] > 0 and info["n_product"] > 0 and info["n_node"] > 0 and info["n_const"] > 0
+    f, g = h.eval_grad(_x(x))
+    h.sync_status()
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+
+
+def test_mixed_fp64(F):
+    inst = mixed_instance(2)
+    x = gen.uniform_points(19, inst.n, 4, dtype=np.float64)
+    h = F.Instance(inst)
+    f, g = h.eval_grad(_x(x, torch.float64))
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-10)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+
+
+@pytest.mark.parametrize("node_r", [8, 16])
+def test_node_all_mode(F, node_r):
+    """OR and XOR through the DFT node kernel reproduce their closed forms."""
+    inst = mixed_instance(3)
+    x = gen.uniform_points(11, inst.n, 5)
+    h = F.Instance(inst, node_all=True, node_r=node_r)
+    assert h.info()["n_product"] == 0 and h.info()["n_clause3"] == 0
+    f, g = h.eval_grad(_x(x))
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4, node_types=(O.OR, O.XOR, O.ATLEAST))
+    assert ef <= 1 and eg <= 1, (ef, eg)
+
+
+def test_paper_form_short_constraints(F):
+    """The paper's literal factors 1 + y w^j with Walsh-derived weights (L <= 24).
+
+    FP64 matches the oracle tightly; in FP32 the node terms b_j prod(1 + y w^j)
+    reach 2^L / N and cancel, so FP32 is only checked for L <= 8, where its error
+    (~5e-7 absolute) is within the node-path allowance; the loss of precision
+    with length is the Conclusion's remark."""
+    rng = np.random.default_rng(9)
+    n = 200
+
+    def build(Lmax):
+        cons = []
+        for L in range(1, Lmax + 1):
+            for K in (1, max(1, L // 2), L):
+                vs = (rng.choice(n, L, replace=False) + 1) * rng.choice([-1, 1], L)
+                cons.append((gen.ATLEAST, K, vs.tolist()))
+            vs = (rng.choice(n, L, replace=False) + 1) * rng.choice([-1, 1], L)
+            cons.append((gen.XOR, L & 1, vs.tolist()))
+        return gen.from_lists(n, cons)
+
+    inst = build(24)
+    x = gen.uniform_points(9, n, 2, dtype=np.float64)
+    h64 = F.Instance(inst, form=F.FFSAT_FORM_PAPER, node_all=True)
+    f, g = h64.eval_grad(_x(x, torch.float64))
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-9)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+    small = build(8)
+    hs = F.Instance(small, form=F.FFSAT_FORM_PAPER, node_all=True)
+    f, g = hs.eval_grad(_x(x))
+    ef, eg = compare(small, x, to_np(f), to_np(g), 1e-4, node_types=(O.OR, O.XOR, O.ATLEAST))
+    assert ef <= 1 and eg <= 1, (ef, eg)
+
+
+def test_weights_and_set_weights(F):
+    inst = mixed_instance(4)
+    x = gen.uniform_points(8, inst.n, 6)
+    h = F.Instance(inst)
+    w2 = np.random.default_rng(1).uniform(0, 3, inst.m)
+    w2[::7] = 0.0
+    h.set_weights(w2)
+    f, g = h.eval_grad(_x(x))
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4, weights=w2)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+
+
+def test_f_only_and_g_only(F):
+    inst = mixed_instance(5)
+    x = gen.uniform_points(6, inst.n, 7)
+    h = F.Instance(inst)
+    f, _ = h.eval_grad(_x(x), want_g=False)
+    _, g = h.eval_grad(_x(x), want_f=False)
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4)
+    assert ef <= 1 and eg <= 1
+
+
+@pytest.mark.parametrize("n", [30000, 70000])
+def test_large_n_shared_memory_modes(F, n):
+    """x and gradient outside shared memory (n beyond the 227 KB budget)."""
+    inst = gen.concat([gen.random_ksat(n, 4 * n, 3, 1), gen.random_xor(n, 40, 10, 60, 1, signs=True),
+                       gen.random_atleast(n, 20, 32, 300, 1)])
+    x = gen.uniform_points(5, n, 1)
+    h = F.Instance(inst)
+    assert h.info()["smem_mode_f32"] == (1 if n == 30000 else 2)
+    f, g = h.eval_grad(_x(x))
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+    x1 = _x(x)
+    h.step(x1, T=1, lr=0.05, restart=False)
+    fs, gs = O.eval_grad(inst, x.astype(np.float64))
+    want = np.clip(x.astype(np.float64) - 0.05 * gs, -1, 1)
+    assert np.max(np.abs(to_np(x1) - want)) < 1e-4 * max(1.0, float(np.abs(gs).max()))
+
+
+def test_plain64(F):
+    inst = mixed_instance(6)
+    x = gen.uniform_points(7, inst.n, 8, dtype=np.float64)
+    h = F.Instance(inst)
+    f, g = h.eval_grad_plain64(_x(x, torch.float64))
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-10)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+
+
+def test_edge_cases(F):
+    # B = 0 is a no-op
+    inst = mixed_instance(7)
+    h = F.Instance(inst)
+    f, g = h.eval_grad(torch.empty(0, inst.n, device="cuda"))
+    assert f.numel() == 0
+    # no constraints
+    e = gen.from_lists(5, [])
+    he = F.Instance(e)
+    f, g = he.eval_grad(_x(gen.uniform_points(3, 5, 0)))
+    assert torch.all(f == 0) and torch.all(g == 0)
+    sat, nun = he.check(_x(gen.uniform_points(3, 5, 0)))
+    assert torch.all(sat == 1) and torch.all(nun == 0)
+    # one variable, constant constraints only
+    c = gen.from_lists(1, [(gen.ATLEAST, 0, [1]), (gen.ATLEAST, 2, [-1])], [2.0, 3.0])
+    hc = F.Instance(c)
+    f, g = hc.eval_grad(_x(np.array([[0.3]], dtype=np.float32)))
+    assert to_np(f)[0] == -2.0 + 3.0 and to_np(g)[0, 0] == 0.0
+
+
+def test_nan_is_reported(F):
+    inst = mixed_instance(8)
+    x = gen.uniform_points(2, inst.n, 0)
+    x[1, 5] = np.nan
+    h = F.Instance(inst)
+    h.eval_grad(_x(x))
+    with pytest.raises(F.FFSatError) as e:
+        h.sync_status()
+    assert e.value.code == -9
+    h.sync_status()  # cleared
+
+
+# ---------------------------------------------------------------------------------------------
+# exact checker: bit-exact against the twin
+# ---------------------------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_check_bit_exact(F, dtype):
+    inst = mixed_instance(10)
+    xs = [gen.corner_points(40, inst.n, 1, zero_frac=0.3), gen.uniform_points(40, inst.n, 2),
+          gen.near_corner_points(40, inst.n, 3)]
+    h = F.Instance(inst)
+    for x in xs:
+        sat, nun = h.check(_x(x, dtype))
+        s2, n2 = O.check(inst, x.astype(np.float64))
+        assert np.array_equal(to_np(sat), s2) and np.array_equal(to_np(nun), n2)
+
+
+def test_check_planted_model(F):
+    inst = gen.cnf_xor_2000(1, planted=True)
+    h = F.Instance(inst)
+    z = inst.planted[None].astype(np.float32)
+    sat, nun = h.check(_x(np.concatenate([z, -z])))
+    assert to_np(sat)[0] == 1 and to_np(nun)[0] == 0
+
+
+# ---------------------------------------------------------------------------------------------
+# step: one projected-GD iteration, restarts, FP64 200-step trajectory
+# ---------------------------------------------------------------------------------------------
+
+
+def test_step_one_iteration_fp32(F):
+    inst = mixed_instance(11)
+    x = gen.uniform_points(13, inst.n, 4)
+    h = F.Instance(inst)
+    xt = _x(x)
+    solved, nun = h.step(xt, T=1, lr=0.1, restart=False)
+    fs, gs = O.eval_grad(inst, x.astype(np.float64))
+    _, A = O.eval_scale(inst, x.astype(np.float64), 1e-2)  # floor on at-least-K literals
+    want = np.clip(x.astype(np.float64) - 0.1 * gs, -1, 1)
+    tol = 0.1 * 1e-4 * np.maximum(np.abs(gs), A) + 1e-7
+    assert np.all(np.abs(to_np(xt) - want) <= tol)
+    s2, n2 = O.check(inst, to_np(xt).astype(np.float64))
+    assert np.array_equal(to_np(solved), s2) and np.array_equal(to_np(nun), n2)
+
+
+def test_step_restart_draws_bit_exact(F):
+    inst = gen.uniform_3sat_100(2)
+    x = gen.uniform_points(24, inst.n, 5)
+    h = F.Instance(inst)
+    xt = _x(x)
+    x_before = None
+    solved, nun = h.step(xt, T=0, lr=0.1, seed=123, epoch=7, b_offset=1000, restart=True)
+    s2, n2 = O.check(inst, x.astype(np.float64))
+    assert np.array_equal(to_np(solved), s2) and np.array_equal(to_np(nun), n2)
+    got = to_np(xt)
+    for b in range(24):
+        if s2[b]:
+            assert np.array_equal(got[b], x[b])
+        else:
+            want = np.array([O.uniform(123, 7, 1000 + b, v) for v in range(inst.n)])
+            assert np.array_equal(got[b].astype(np.float64), want)
+
+
+def test_step_fp64_200_iterations_matches_oracle(F):
+    """Config 1: 3-SAT n=100, m=426, B=32, 200 steps of lr 0.1 in FP64."""
+    inst = gen.uniform_3sat_100(0)
+    x = gen.uniform_points(32, inst.n, 0, dtype=np.float64)
+    h = F.Instance(inst)
+    xt = _x(x, torch.float64)
+    solved, nun = h.step(xt, T=200, lr=0.1, seed=1, restart=False)
+    xo, so, no = O.step(inst, x, T=200, lr=0.1, seed=1, restart=False)
+    assert np.max(np.abs(to_np(xt) - xo)) < 1e-9
+    assert np.array_equal(to_np(solved), so) and np.array_equal(to_np(nun), no)
+
+
+# ---------------------------------------------------------------------------------------------
+# full-size workloads, launch configuration of the benchmark, sampled points
+# ---------------------------------------------------------------------------------------------
+
+
+def test_cnf_xor_2000_full(F):
+    inst = gen.cnf_xor_2000(0)
+    B = 256
+    x = gen.uniform_points(B, inst.n, 0)
+    h = F.Instance(inst)
+    f, g = h.eval_grad(_x(x))
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+    # FP64 path on the same points
+    f64, g64 = h.eval_grad(_x(x, torch.float64))
+    ef, eg = compare(inst, x, to_np(f64), to_np(g64), 1e-10, points=np.arange(0, B, 16))
+    assert ef <= 1 and eg <= 1
+
+
+def test_cnf_card_20000_full_sampled(F):
+    inst = gen.cnf_card_20000(0)
+    B = 1024
+    x = gen.uniform_points(B, inst.n, 0)
+    h = F.Instance(inst)
+    f, g = h.eval_grad(_x(x))
+    pts = np.array([0, 1, 511, 777, 1023])
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4, points=pts)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+
+
+def test_cnf_card_near_corner(F):
+    inst = gen.cnf_card_20000(1)
+    x = gen.near_corner_points(4, inst.n, 1)
+    h = F.Instance(inst)
+    f, g = h.eval_grad(_x(x))
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+
+
+@pytest.mark.parametrize("name", list(gen.RQ1_SHAPES))
+def test_rq1_shapes(F, name):
+    inst = gen.rq1(name)
+    x = gen.uniform_points(64, inst.n, 2)
+    h = F.Instance(inst)
+    f, g = h.eval_grad(_x(x))
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4)
+    assert ef <= 1 and eg <= 1, (ef, eg)
