@@ -162,6 +162,30 @@ int ffsat_eval_grad_plain64(ffsat_instance *inst, int32_t B, const double *x, do
 int ffsat_step(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, const ffsat_step_args *args,
                uint8_t *solved, int32_t *n_unsat, void *stream);
 
+/* Size of the scratch that ffsat_step_noalloc uses instead of allocating. */
+#define FFSAT_STATIC_SCRATCH_BYTES (32u << 20)
+
+/* ffsat_step without any device allocation; the paper has no counterpart.
+ * Some callers cannot call cudaMalloc: a host that hands all device memory to
+ * its own pool allocator, or a latency-critical loop that cannot accept the
+ * implicit device synchronisation of an allocation.  ffsat_step allocates a
+ * gradient scratch buffer of B * n values (and keeps it with the instance) when
+ * a point's x and gradient do not fit in shared memory (ffsat_info.smem_mode
+ * 1 or 2); this entry point uses instead a buffer of FFSAT_STATIC_SCRATCH_BYTES
+ * that is reserved statically in the library's device image, so every GPU that
+ * loads the library holds it until the process exits.
+ *  - Same arguments, results and errors as ffsat_step.
+ *  - Returns FFSAT_ERR_ARG when the instance needs scratch and
+ *    B * n * sizeof(dtype) exceeds FFSAT_STATIC_SCRATCH_BYTES.
+ *  - The first call on a device looks up the buffer's device address (with that
+ *    device current) and caches it; make that first call before any stream
+ *    capture.
+ *  - Every call shares the one buffer and the kernel clears the part it uses
+ *    before accumulating.  Calls whose kernels overlap on the GPU (other streams,
+ *    other instances, other threads) race on it: order them. */
+int ffsat_step_noalloc(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, const ffsat_step_args *args,
+                       uint8_t *solved, int32_t *n_unsat, void *stream);
+
 /* Exact checker (Alg. 1, line 5, evaluated on integers rather than through F):
  * sat[b] = 1 iff sgn(x_b) satisfies every constraint, regardless of weights;
  * n_unsat[b] = number of violated constraints.  Either output may be NULL. */

@@ -971,6 +971,50 @@ int ffsat_step(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat
     return FFSAT_OK;
 }
 
+int ffsat_step_noalloc(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat_step_args *args,
+                       uint8_t *solved, int32_t *n_unsat, void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!I || !args) return fail(FFSAT_ERR_ARG, "NULL argument");
+    if (B < 0 || args->T < 0) return fail(FFSAT_ERR_ARG, "B and T must be >= 0");
+    if (!std::isfinite(args->lr)) return fail(FFSAT_ERR_ARG, "lr must be finite");
+    int rc = check_dtype(dtype);
+    if (rc) return rc;
+    if (B == 0) return FFSAT_OK;
+    if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
+    CUDA_TRY(cudaSetDevice(I->device));
+    const bool f64 = dtype == FFSAT_F64;
+    const int mode = f64 ? I->smem_mode64 : I->smem_mode32;
+    const size_t elem = f64 ? sizeof(double) : sizeof(float);
+    FusedArgs a{};
+    a.B = B;
+    a.mode = MODE_STEP;
+    a.x_in = x;
+    a.x_out = x;
+    a.solved = solved;
+    a.n_unsat = n_unsat;
+    a.sp.T = args->T;
+    a.sp.restart = args->restart;
+    a.sp.lr = args->lr;
+    a.sp.seed = args->seed;
+    a.sp.epoch = args->epoch;
+    a.sp.b_offset = args->b_offset;
+    if (mode != SMEM_FULL && mode != SMEM_RES) {
+        const size_t need = (size_t)B * (size_t)I->n * elem;
+        if (need > (size_t)FFSAT_STATIC_SCRATCH_BYTES)
+            return fail(FFSAT_ERR_ARG, "B * n * %zu = %zu bytes of gradient scratch exceed the static %u bytes",
+                        elem, need, (unsigned)FFSAT_STATIC_SCRATCH_BYTES);
+        void *p = nullptr;
+        CUDA_TRY(static_scratch(I->device, &p));
+        a.g_scratch = p;
+    }
+    const DevView &V = f64 ? I->V64 : I->V32;
+    CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(B),
+                                                          static_cast<cudaStream_t>(stream), false));
+    t_launches = 1;
+    return FFSAT_OK;
+}
+
 int ffsat_check(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, uint8_t *sat, int32_t *n_unsat,
                 void *stream) {
     t_err.clear();

@@ -118,6 +118,10 @@ FFSAT_FUSED_LAUNCHER(fused_f64_r0);
 FFSAT_FUSED_LAUNCHER(fused_f64_r8);
 FFSAT_FUSED_LAUNCHER(fused_f64_r16);
 
+// Device address of the statically reserved scratch (FFSAT_STATIC_SCRATCH_BYTES)
+// on `device`, which must be current; looked up on the first call per device.
+cudaError_t static_scratch(int device, void **ptr);
+
 // Exact checker: one CTA per point.
 cudaError_t launch_check(const DevView &V, bool f64, int B, const void *x, uint8_t *sat, int32_t *n_unsat,
                          cudaStream_t s);

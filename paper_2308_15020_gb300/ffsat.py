@@ -21,6 +21,7 @@ FFSAT_OR, FFSAT_XOR, FFSAT_ATLEAST = 0, 1, 2
 FFSAT_F32, FFSAT_F64 = 0, 1
 FFSAT_FORM_STABLE, FFSAT_FORM_PAPER = 0, 1
 FFSAT_MAX_LEN = 512
+FFSAT_STATIC_SCRATCH_BYTES = 32 << 20
 
 ERRORS = {
     0: "FFSAT_OK",
@@ -44,6 +45,7 @@ SYMBOLS = (
     "ffsat_eval_grad",
     "ffsat_eval_grad_plain64",
     "ffsat_step",
+    "ffsat_step_noalloc",
     "ffsat_check",
     "ffsat_sync_status",
     "ffsat_instance_info",
@@ -106,6 +108,8 @@ def lib():
         L.ffsat_eval_grad_plain64.restype = C.c_int
         L.ffsat_step.argtypes = [_vp, C.c_int32, _vp, C.c_int32, C.POINTER(StepArgs), _vp, _vp, _vp]
         L.ffsat_step.restype = C.c_int
+        L.ffsat_step_noalloc.argtypes = [_vp, C.c_int32, _vp, C.c_int32, C.POINTER(StepArgs), _vp, _vp, _vp]
+        L.ffsat_step_noalloc.restype = C.c_int
         L.ffsat_check.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
         L.ffsat_check.restype = C.c_int
         L.ffsat_sync_status.argtypes = [_vp, _vp]
@@ -250,6 +254,22 @@ class Instance:
         a = StepArgs(int(T), int(restart), float(lr), int(seed) & (2**64 - 1), int(epoch), int(b_offset))
         _check(lib().ffsat_step(self.handle, B, x.data_ptr(), _dtype_code(x), C.byref(a), solved.data_ptr(),
                                 n_unsat.data_ptr(), _stream(stream)))
+        return solved, n_unsat
+
+    def step_noalloc(self, x, T: int, lr: float, seed: int = 0, epoch: int = 0, b_offset: int = 0,
+                     restart: bool = True, solved=None, n_unsat=None, stream=None):
+        """``step`` through ``ffsat_step_noalloc``: no device allocation, static scratch."""
+        import torch
+
+        _need_cuda_contig(x, "x")
+        B = x.shape[0]
+        if solved is None:
+            solved = torch.empty(B, dtype=torch.uint8, device=x.device)
+        if n_unsat is None:
+            n_unsat = torch.empty(B, dtype=torch.int32, device=x.device)
+        a = StepArgs(int(T), int(restart), float(lr), int(seed) & (2**64 - 1), int(epoch), int(b_offset))
+        _check(lib().ffsat_step_noalloc(self.handle, B, x.data_ptr(), _dtype_code(x), C.byref(a), solved.data_ptr(),
+                                        n_unsat.data_ptr(), _stream(stream)))
         return solved, n_unsat
 
     def check(self, x, sat=None, n_unsat=None, stream=None):
