@@ -43,6 +43,8 @@ WORKLOADS = {
     "cnf_xor_n2000": (gen.cnf_xor_2000, 256, "f32", 200, 0.1),
     "cnf_card_n20000": (gen.cnf_card_20000, 1024, "f32", 4, 0.1),
     "3sat_n100": (gen.uniform_3sat_100, 32, "f64", 200, 0.1),
+    # 64 uneven instances (n log-uniform 500..50000), B points each, one batch launch per step
+    "uneven_batch": (gen.uneven_batch, 128, "f32", 2, 0.1),
 }
 
 FP32_LANES_PER_SM = 128
@@ -119,11 +121,17 @@ class ClockSampler:
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
 
+    def mark(self):
+        """Only samples taken after this call count (the timed region)."""
+        self.fh.flush()
+        self.t_mark = time.time()
+
     def start(self):
+        self.t_mark = 0.0
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         try:
             self.fh = open(self.path, "w")
-            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu=timestamp,{self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
@@ -140,16 +148,24 @@ class ClockSampler:
         self.fh.close()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                ts = self.t_mark
+            if ts < self.t_mark - 0.25:
+                continue
+            try:
+                sm.append(float(parts[2]))
+                smax.append(float(parts[3]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+            for nm, v in zip(names, parts[6:10]):
                 if v.lower() == "active":
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
@@ -210,6 +226,8 @@ def run_reference(args, rank: int, world: int):
     build, B, dt_name, T, lr = WORKLOADS[args.workload]
     T = args.T or T
     inst = build(0)
+    if isinstance(inst, list):  # a batch workload: time the median instance
+        inst = inst[len(inst) // 2]
     B_s, T_s = calibrate_sample(inst, B, T, lr, target_s=args.ref_seconds)
     xs = gen.uniform_points(B_s, inst.n, 0, dtype=np.float64)
     for _ in range(args.warmup):
@@ -252,6 +270,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     build, B, dtname, T, lr = WORKLOADS[args.workload]
     T = args.T or T
     B = args.B or B
+    if args.workload == "uneven_batch":
+        return run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr)
     inst = build(0)
     st = instance_stats(inst)
     h = ffsat.Instance(inst)
@@ -272,21 +292,25 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                stream=stream)
         epoch[0] += 1
 
+    # the clock sampler starts before the warm-up so that its start-up is not in the timed region
+    clocks = ClockSampler(visible_device_index(local_rank)) if rank == 0 else None
+    if clocks:
+        clocks.start()
     for _ in range(max(args.warmup, 3)):
         flush.zero_()
         one_step()
     torch.cuda.synchronize()
     h.sync_status()
     launches_per_step = ffsat.last_launch_count()
+    time.sleep(0.5)
 
     # ---- device-timed region ----
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    clocks = ClockSampler(visible_device_index(local_rank)) if rank == 0 else None
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     if clocks:
-        clocks.start()
+        clocks.mark()
     for s, e in evs:
         flush.zero_()
         s.record(stream)
@@ -371,6 +395,131 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
         "kernel_source_hash": kernel_source_hash(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
+    """Configuration 4: all instances' points in one persistent launch per step."""
+    import torch
+
+    from paper_2308_15020_gb300 import ffsat
+
+    insts = build(0)
+    hs = [ffsat.Instance(i) for i in insts]
+    bt = ffsat.Batch(hs)
+    xs_host = [torch.from_numpy(gen.uniform_points(B, i.n, 2000 + 97 * k + rank)).pin_memory()
+               for k, i in enumerate(insts)]
+    xs = [x.cuda() for x in xs_host]
+    solved = [torch.empty(B, dtype=torch.uint8, device="cuda") for _ in insts]
+    nun = [torch.empty(B, dtype=torch.int32, device="cuda") for _ in insts]
+    offs = [rank * B * len(insts) + k * B for k in range(len(insts))]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    epoch = [0]
+
+    def one_step():
+        bt.step(xs, T=T, lr=lr, seed=7, epoch=epoch[0], restart=True, b_offsets=offs, solved=solved, n_unsat=nun,
+                stream=stream)
+        epoch[0] += 1
+
+    clocks = ClockSampler(visible_device_index(local_rank)) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    for _ in range(max(args.warmup, 3)):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize()
+    for h in hs:
+        h.sync_status()
+    launches_per_step = ffsat.last_launch_count()
+    time.sleep(0.5)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.mark()
+    for s, e in evs:
+        flush.zero_()
+        s.record(stream)
+        one_step()
+        e.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop() if clocks else None
+    total_ms = sum(s.elapsed_time(e) for s, e in evs)
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    nnz = sum(i.nnz for i in insts)
+    work = B * nnz * T
+    value = world * work * args.steps / (total_ms / 1e3)
+    # end to end: inputs from pinned host memory, flags back
+    solved_h = [torch.empty(B, dtype=torch.uint8).pin_memory() for _ in insts]
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for x, xh in zip(xs, xs_host):
+            x.copy_(xh, non_blocking=True)
+        one_step()
+        for sh, sd in zip(solved_h, solved):
+            sh.copy_(sd, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_total = sum(e2e_ms)
+    if dist:
+        t = torch.tensor([e2e_total], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks, peak_src = load_peaks()
+    flops = bytes_ = 0.0
+    for i in insts:
+        fl, by, _ = algorithmic_work(instance_stats(i), B, T)
+        flops += fl
+        bytes_ += by
+    launch_s = (total_ms / args.steps) / 1e3
+    n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": flops / launch_s / 1e12 / peak,
+            "peak_source": f"FP32 FMA lanes x 2 x {sm_max:.0f} MHz (max SM clock, {peak_src} peaks file)",
+            "algorithmic_per_launch": flops, "traffic": None}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        sys.path.insert(0, os.path.join(ROOT, "oracle"))
+        import oracle as O
+
+        k = len(insts) // 2
+        xs_s = gen.uniform_points(O.max_threads(), insts[k].n, 0, dtype=np.float64)
+        rate, dt, threads = oracle_rate(insts[k], xs_s, 2, lr)
+        cpu = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{xs_s.shape[0]} points x 2 PGD iterations of instance {k} (n={insts[k].n}), {dt:.1f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded generator)",
+        "config": {"workload": args.workload, "instances": len(insts), "B_per_instance": B,
+                   "n_total": int(sum(i.n for i in insts)), "nnz_total": int(nnz), "pgd_iters_per_step": T,
+                   "lr": lr, "launch": "one persistent batch kernel per step",
+                   "l2": "flushed before every timed step (256 MiB write)",
+                   "parallelism": f"replicas x{world} (points sharded, no collective)"},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": world * work * args.steps / (e2e_total / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in xs_host)),
+                "d2h_bytes_per_step": int(B * len(insts))},
+        "gpu_launches": launches_per_step * args.steps, "clocks": clk, "kernel_source_hash": kernel_source_hash(),
     }
     print(json.dumps(line), flush=True)
     if dist:

@@ -107,6 +107,8 @@ typedef struct ffsat_info {
     int32_t threads_f32;   /* threads per CTA of the fused kernel */
     int64_t node_lane_work; /* sum over node constraints of nodes x (lanes x R) per point */
     int64_t device_bytes;  /* device memory held by the instance */
+    int32_t autotuned;     /* 1 if node_r was chosen by timing candidates at load */
+    float autotune_us[2];  /* measured eval time of the candidates (node R 16/12, node R 8), microseconds */
 } ffsat_info;
 
 /* Fill `opt` with the defaults (stable form, closed forms for OR/XOR,
@@ -191,6 +193,43 @@ int ffsat_step_noalloc(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, 
  * n_unsat[b] = number of violated constraints.  Either output may be NULL. */
 int ffsat_check(ffsat_instance *inst, int32_t B, const void *x, int32_t dtype, uint8_t *sat, int32_t *n_unsat,
                 void *stream);
+
+/* ---- several instances of uneven size in one launch ---------------------------------- */
+
+typedef struct ffsat_batch ffsat_batch;
+
+/* Per-instance buffers of a batch call (all device pointers of the call's dtype). */
+typedef struct ffsat_batch_io {
+    int32_t B;         /* points of this instance (>= 0) */
+    int32_t pad;
+    void *x;           /* [B, n]: read by eval; updated in place by step */
+    double *f;         /* eval: [B] or NULL */
+    void *g;           /* eval: [B, n] or NULL */
+    uint8_t *solved;   /* step: [B] or NULL */
+    int32_t *n_unsat;  /* step: [B] or NULL */
+    uint64_t b_offset; /* step: global index of point 0 of this instance (restart key) */
+} ffsat_batch_io;
+
+/* Group `count` loaded instances (same device) for single-launch evaluation: one
+ * persistent kernel whose CTAs pull (instance, point) items, longest first, from a
+ * device counter; every point runs exactly as in ffsat_eval_grad / ffsat_step of
+ * its instance (same shared-memory mode and constraint layout).  The instances
+ * must outlive the batch.  Configuration 4 of the benchmark ("uneven instances
+ * in one launch") is this call. */
+int ffsat_batch_create(ffsat_instance *const *insts, int32_t count, ffsat_batch **out);
+
+/* ffsat_eval_grad for every instance of the batch in one launch (plus one
+ * memset of the work counter).  io: host array of `count` entries. */
+int ffsat_batch_eval_grad(ffsat_batch *bt, const ffsat_batch_io *io, int32_t dtype, void *stream);
+
+/* ffsat_step for every instance of the batch in one launch; args->b_offset is
+ * ignored in favour of io[k].b_offset.  Uses batch-owned gradient scratch for
+ * instances whose x and gradient do not fit in shared memory. */
+int ffsat_batch_step(ffsat_batch *bt, const ffsat_batch_io *io, int32_t dtype, const ffsat_step_args *args,
+                     void *stream);
+
+/* Release the batch (not its instances). */
+void ffsat_batch_free(ffsat_batch *bt);
 
 /* Synchronise `stream`, read and clear the instance's device status word:
  * FFSAT_OK, FFSAT_ERR_NAN or FFSAT_ERR_DEVICE. */

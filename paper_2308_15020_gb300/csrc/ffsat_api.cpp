@@ -138,7 +138,7 @@ struct ffsat_instance {
     std::vector<int32_t> seg_lits;
     int n_node_seg = 0;
     int32_t pad_node = 0;        // padding literal of node segments (dummy n or n + 1)
-    int nr[2] = {0, 0};          // node R of image 0 (FP32) and image 1 (FP64)
+    int nr[3] = {0, 0, 0};       // node R of each image
     std::vector<double> clause_wd;
     std::vector<double> seg_wd;
     std::vector<double> cons_wd;
@@ -147,11 +147,13 @@ struct ffsat_instance {
     float fix_s1 = 1.0f, fix_s2 = 1.0f, fix_i1 = 1.0f, fix_i12 = 1.0f;
     std::vector<int64_t> row_ptr;  // host copy of the CSR (fixed-point scales)
     std::vector<int32_t> lits_in;
-    // resident images per dtype (index 0: FP32 task list, 1: FP64 task list)
-    std::vector<int4> tasks[2];
-    std::vector<int4> image[2];
-    int32_t img_off[2][4] = {{0}};  // tasks, clauses, segmeta, seg_lits (int4 units)
-    size_t off_image[2] = {0, 0};
+    // resident images (index 0: FP32 task list, 1: FP64 task list, 2: the FP32
+    // autotune candidate that lost, kept so that set_weights stays consistent)
+    int n_images = 2;
+    std::vector<int4> tasks[3];
+    std::vector<int4> image[3];
+    int32_t img_off[3][4] = {{0}};  // tasks, clauses, segmeta, seg_lits (int4 units)
+    size_t off_image[3] = {0, 0, 0};
     // device
     unsigned char *d_arena = nullptr;
     size_t arena_bytes = 0;
@@ -215,6 +217,20 @@ inline int32_t pack_lit(int32_t l) {
 // Lanes per constraint segment: the smallest power of two G with G * R >= L.
 inline int seg_lanes(int L, int R) { return std::max(1, pow2_at_least((L + R - 1) / R)); }
 
+// Literals per lane of a node segment.  A kernel built for node R = 16 also
+// runs 12 literals per lane; per segment the host picks the shape with the
+// smaller modelled cost per node, G * (12 NR + 12 + 10 log2 G) lane
+// instructions (12 per literal slot, butterfly and per-node overhead).
+inline int node_nr(int L, int nr_max) {
+    if (nr_max < 16) return nr_max;
+    auto cost = [&](int nr) {
+        const int G = seg_lanes(L, nr);
+        if (G > 32) return 1e30;
+        return (double)G * (12.0 * nr + 12.0 + 10.0 * std::log2((double)G));
+    };
+    return cost(12) < cost(16) ? 12 : 16;
+}
+
 // Per-constraint FE of constant constraints (cardinality with K <= 0 or K > L).
 inline bool constant_value(int type, int param, int L, double &fe) {
     if (type != FFSAT_ATLEAST) return false;
@@ -258,13 +274,23 @@ void build_table(int type, int param, int L, int form, std::vector<float> &tf, s
             br = 0.5 * (1.0 - wr);
             bi = -0.5 * wi;
         }
-        // c_j = (mult / N) sum_k coef[k] omega^{-j k}
+        // c_j = (mult / N) sum_k coef[k] omega^{-j k}: the powers come from a
+        // rotation recurrence, re-anchored on exact values every 32 terms
         double cr = 0.0, ci = 0.0;
+        const double rot_r = std::cos(two_pi * (double)j / (double)N), rot_i = std::sin(two_pi * (double)j / (double)N);
+        double zr = 1.0, zi = 0.0;
         for (int k = 0; k <= L; ++k) {
-            const long long jk = ((long long)j * k) % N;
-            const double ph = two_pi * (double)jk / (double)N;
-            cr += coef[k] * std::cos(ph);
-            ci += coef[k] * std::sin(ph);
+            if ((k & 31) == 0) {
+                const long long jk = ((long long)j * k) % N;
+                const double ph = two_pi * (double)jk / (double)N;
+                zr = std::cos(ph);
+                zi = std::sin(ph);
+            }
+            cr += coef[k] * zr;
+            ci += coef[k] * zi;
+            const double nr = zr * rot_r - zi * rot_i;
+            zi = zr * rot_i + zi * rot_r;
+            zr = nr;
         }
         cr *= mult / N;
         ci *= mult / N;
@@ -305,15 +331,18 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
         const int end = first + count;
         while (i < end) {
             const int L = seg_len[i];
-            const int G = seg_lanes(L, R);
+            const int nr = kind == TASK_NODE ? node_nr(L, R) : R;
+            const int G = seg_lanes(L, nr);
             const int S = 32 / G;
             int k = 0;
             while (k < S && i + k < end) {
-                if (seg_lanes(seg_len[i + k], R) != G) break;
+                const int Lk = seg_len[i + k];
+                const int nk = kind == TASK_NODE ? node_nr(Lk, R) : R;
+                if (nk != nr || seg_lanes(Lk, nk) != G) break;
                 ++k;
             }
             const int J = kind == TASK_NODE ? (L + 1) / 2 + 1 : 0;
-            ts.tasks.push_back(make_int4(kind | (G << 8), i, k, J));
+            ts.tasks.push_back(make_int4(kind | (G << 8) | (nr << 16), i, k, J));
             i += k;
         }
     };
@@ -433,7 +462,7 @@ void build_image(ffsat_instance *I, int k) {
     for (size_t s = 0; s < I->seg_info.size(); ++s) {
         const int4 si = I->seg_info[s];
         const bool node = (int)s < I->n_node_seg;
-        const int R = node ? nr : kProdR;
+        const int R = node ? node_nr(si.y, nr) : kProdR;
         const int G = seg_lanes(si.y, R);
         const int32_t pad = node ? I->pad_node : I->n;
         const int32_t off = (int32_t)lits.size();
@@ -494,8 +523,11 @@ void bank_order(std::vector<int4> &cls, std::vector<int32_t> &cid) {
     for (size_t i = 0; i < m; ++i) {
         const auto b = banks(i);
         int found = -1;
-        for (int sz = 31; sz >= 0 && found < 0; --sz) {
+        int probes = 0;
+        constexpr int kMaxProbe = 256;  // groups examined per clause (fullest first)
+        for (int sz = 31; sz >= 0 && found < 0 && probes < kMaxProbe; --sz) {
             for (int32_t g : by_size[sz]) {
+                if (++probes > kMaxProbe) break;
                 uint8_t need[32] = {0};
                 bool ok = true;
                 for (int q = 0; q < 3 && ok; ++q) ok = cap[g][b[q]] > need[b[q]]++;
@@ -517,7 +549,7 @@ void bank_order(std::vector<int4> &cls, std::vector<int32_t> &cid) {
     for (int32_t i : left) {
         const auto b = banks(i);
         int best = -1, best_cost = 1 << 30;
-        for (size_t g = 0; g < G; ++g) {
+        for (size_t g = 0; g < G && best_cost > 0; ++g) {
             if (size[g] >= 32) continue;
             int cost = 0;
             uint8_t need[32] = {0};
@@ -587,6 +619,92 @@ void bank_order(std::vector<int4> &cls, std::vector<int32_t> &cid) {
     }
     cls.swap(out);
     cid.swap(out_id);
+}
+
+// DevView of image k on top of the shared part V.
+DevView view_for_image(ffsat_instance *P, const DevView &V, int k) {
+    DevView W = V;
+    const int4 *img = reinterpret_cast<const int4 *>(P->d_arena + P->off_image[k]);
+    W.res_image = img;
+    W.res_int4 = (int32_t)P->image[k].size();
+    W.res_off_tasks = P->img_off[k][0];
+    W.res_off_clauses = P->img_off[k][1];
+    W.res_off_segmeta = P->img_off[k][2];
+    W.res_off_lits = P->img_off[k][3];
+    W.tasks = img + W.res_off_tasks;
+    W.clauses = img + W.res_off_clauses;
+    W.segmeta = img + W.res_off_segmeta;
+    W.seg_lits = reinterpret_cast<const int32_t *>(img + W.res_off_lits);
+    W.n_task = (int32_t)P->tasks[k].size();
+    return W;
+}
+
+// Time the FP32 evaluation of images 0 (node R 16/12) and 2 (node R 8) on a
+// probe batch of one point per SM and keep the faster as image 0.
+int autotune(ffsat_instance *P, const DevView &V) {
+    const int B = P->num_sms;
+    const size_t elems = (size_t)B * (size_t)P->n;
+    std::vector<float> hx(elems);
+    uint64_t st = 0x9E3779B97F4A7C15ull;
+    for (size_t i = 0; i < elems; ++i) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        hx[i] = (float)((double)(st >> 40) / (double)(1ull << 23) - 1.0);
+    }
+    float *dx = nullptr, *dg = nullptr;
+    double *df = nullptr;
+    CUDA_TRY(cudaMalloc(&dx, elems * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&dg, elems * sizeof(float)));
+    CUDA_TRY(cudaMalloc(&df, (size_t)B * sizeof(double)));
+    CUDA_TRY(cudaMemcpy(dx, hx.data(), elems * sizeof(float), cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CUDA_TRY(cudaEventCreate(&e0));
+    CUDA_TRY(cudaEventCreate(&e1));
+    float us[2] = {0.f, 0.f};
+    DevView cand[2] = {P->V32, view_for_image(P, V, 2)};
+    int nr[2] = {P->nr[0], P->nr[2]};
+    int mode[2];
+    size_t smem[2];
+    mode[0] = P->smem_mode32;
+    smem[0] = P->smem32;
+    mode[1] = smem_mode_for(P->n, sizeof(float), P->image[2].size() * sizeof(int4), P->max_smem, smem[1]);
+    FusedArgs a{};
+    a.B = B;
+    a.mode = MODE_EVAL;
+    a.x_in = dx;
+    a.f = df;
+    a.g = dg;
+    for (int c = 0; c < 2; ++c) {
+        CUDA_TRY(launcher_for(false, nr[c])(cand[c], mode[c], a, smem[c], 0, 0, true));
+        for (int w = 0; w < 2; ++w) CUDA_TRY(launcher_for(false, nr[c])(cand[c], mode[c], a, smem[c], B, 0, false));
+        CUDA_TRY(cudaEventRecord(e0, 0));
+        for (int r = 0; r < 5; ++r) CUDA_TRY(launcher_for(false, nr[c])(cand[c], mode[c], a, smem[c], B, 0, false));
+        CUDA_TRY(cudaEventRecord(e1, 0));
+        CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        us[c] = 1000.f * ms / 5.f;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(dx);
+    cudaFree(dg);
+    cudaFree(df);
+    CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int32_t)));
+    if (us[1] < us[0]) {
+        std::swap(P->image[0], P->image[2]);
+        std::swap(P->tasks[0], P->tasks[2]);
+        std::swap(P->nr[0], P->nr[2]);
+        std::swap(P->off_image[0], P->off_image[2]);
+        for (int q = 0; q < 4; ++q) std::swap(P->img_off[0][q], P->img_off[2][q]);
+        P->V32 = view_for_image(P, V, 0);
+        P->nr32 = P->nr[0];
+        P->smem_mode32 = mode[1];
+        P->smem32 = smem[1];
+    }
+    P->info.autotuned = 1;
+    P->info.autotune_us[0] = us[0];
+    P->info.autotune_us[1] = us[1];
+    return FFSAT_OK;
 }
 
 }  // namespace
@@ -745,6 +863,16 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     P->tasks[1] = ts64.tasks;
     build_image(P, 0);
     build_image(P, 1);
+    // autotune candidate: node R 8 against the default 16/12 family (FP32)
+    const bool tune = opt.autotune && !node_c.empty() && opt.node_r == 0 && max_node_len <= 8 * 32;
+    if (tune) {
+        TaskSet ts8;
+        build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, 8, ts8);
+        P->n_images = 3;
+        P->nr[2] = 8;
+        P->tasks[2] = ts8.tasks;
+        build_image(P, 2);
+    }
 
     // ---- device ----
     int dev = opt.device;
@@ -755,8 +883,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     CUDA_TRY(cudaDeviceGetAttribute(&P->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
 
     Arena A;
-    P->off_image[0] = A.put(P->image[0]);
-    P->off_image[1] = A.put(P->image[1]);
+    for (int k = 0; k < P->n_images; ++k) P->off_image[k] = A.put(P->image[k]);
     P->off_clause_wd = A.put(P->clause_wd);
     P->off_seg_wd = A.put(P->seg_wd);
     const size_t o_tf = A.put(tab_f), o_td = A.put(tab_d);
@@ -796,22 +923,8 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     V.cons_tab = reinterpret_cast<const int32_t *>(base + o_ctab);
     V.cons_wd = reinterpret_cast<const double *>(base + P->off_cons_wd);
     V.status = P->d_status;
-    for (int k = 0; k < 2; ++k) {
-        DevView &W = k == 0 ? P->V32 : P->V64;
-        W = V;
-        const int4 *img = reinterpret_cast<const int4 *>(base + P->off_image[k]);
-        W.res_image = img;
-        W.res_int4 = (int32_t)P->image[k].size();
-        W.res_off_tasks = P->img_off[k][0];
-        W.res_off_clauses = P->img_off[k][1];
-        W.res_off_segmeta = P->img_off[k][2];
-        W.res_off_lits = P->img_off[k][3];
-        W.tasks = img + W.res_off_tasks;
-        W.clauses = img + W.res_off_clauses;
-        W.segmeta = img + W.res_off_segmeta;
-        W.seg_lits = reinterpret_cast<const int32_t *>(img + W.res_off_lits);
-        W.n_task = (int32_t)P->tasks[k].size();
-    }
+    P->V32 = view_for_image(P, V, 0);
+    P->V64 = view_for_image(P, V, 1);
     P->d_node_ids = reinterpret_cast<int32_t *>(base + o_nid);
     P->d_closed_ids = reinterpret_cast<int32_t *>(base + o_cid);
     P->n_node_ids = (int32_t)node_c.size();
@@ -824,6 +937,11 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     FusedArgs dummy{};
     CUDA_TRY(launcher_for(false, nr32)(P->V32, P->smem_mode32, dummy, P->smem32, 0, 0, true));
     CUDA_TRY(launcher_for(true, nr64)(P->V64, P->smem_mode64, dummy, P->smem64, 0, 0, true));
+    if (tune) {
+        rc = autotune(P, V);
+        if (rc != FFSAT_OK) return rc;
+        nr32 = P->nr32;
+    }
 
     ffsat_info &inf = P->info;
     inf.n = n_vars;
@@ -834,14 +952,14 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     inf.n_node = (int32_t)node_c.size();
     inf.n_const = (int32_t)const_c.size();
     inf.n_tables = (int32_t)tab_index.size();
-    inf.n_tasks = (int32_t)ts32.tasks.size();
+    inf.n_tasks = (int32_t)P->tasks[0].size();
     inf.node_r = nr32;
     inf.smem_mode_f32 = P->smem_mode32;
     inf.smem_mode_f64 = P->smem_mode64;
     inf.threads_f32 = fused_threads(false, nr32);
     int64_t lane_work = 0;
-    for (const int4 &t : ts32.tasks)
-        if ((t.x & 0xff) == TASK_NODE) lane_work += (int64_t)t.w * 32 * nr32;
+    for (const int4 &t : P->tasks[0])
+        if ((t.x & 0xff) == TASK_NODE) lane_work += (int64_t)t.w * 32 * ((t.x >> 16) & 0xff);
     inf.node_lane_work = lane_work;
     inf.device_bytes = (int64_t)P->arena_bytes;
 
@@ -858,7 +976,7 @@ int ffsat_set_weights(ffsat_instance *I, const double *weights) {
     fill_weights(I);
     CUDA_TRY(cudaSetDevice(I->device));
     unsigned char *base = I->d_arena;
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < I->n_images; ++k) {
         build_image(I, k);
         CUDA_TRY(cudaMemcpy(base + I->off_image[k], I->image[k].data(), I->image[k].size() * sizeof(int4), cudaMemcpyHostToDevice));
     }
@@ -1029,6 +1147,211 @@ int ffsat_check(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, uint
     CUDA_TRY(launch_check(I->V32, dtype == FFSAT_F64, B, x, sat, n_unsat, static_cast<cudaStream_t>(stream)));
     t_launches = 1;
     return FFSAT_OK;
+}
+
+}  // extern "C"
+
+struct ffsat_batch {
+    int device = 0;
+    int num_sms = 0;
+    std::vector<ffsat_instance *> insts;
+    int node_r[2] = {0, 0};      // batch-kernel variant per real type (0 or 16)
+    size_t smem[2] = {0, 0};
+    int grid[2] = {0, 0};
+    std::vector<BatchInst> h_insts;  // last table uploaded (per real type: re-uploaded when it changes)
+    int h_insts_dtype = -1;
+    BatchInst *d_insts = nullptr;
+    int *d_counter = nullptr;
+    int2 *d_items = nullptr;
+    size_t items_cap = 0;
+    int n_items = 0;
+    std::vector<int32_t> items_B;  // B per instance of the cached item list
+    void *d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+namespace {
+
+// Items (instance, point), longest first by a per-point cost estimate; cached
+// while the per-instance point counts stay the same.
+int batch_items(ffsat_batch *bt, const ffsat_batch_io *io, cudaStream_t s) {
+    const int K = (int)bt->insts.size();
+    std::vector<int32_t> Bs(K);
+    for (int k = 0; k < K; ++k) Bs[k] = io[k].B;
+    if (Bs == bt->items_B && bt->d_items) return FFSAT_OK;
+    std::vector<std::pair<double, int>> order(K);
+    for (int k = 0; k < K; ++k) {
+        const ffsat_info &inf = bt->insts[k]->info;
+        const double cost = (double)inf.node_lane_work * 12.0 / 32.0 + (double)inf.nnz * 2.0 + (double)inf.n;
+        order[k] = {-cost, k};
+    }
+    std::sort(order.begin(), order.end());
+    std::vector<int2> items;
+    for (const auto &o : order)
+        for (int b = 0; b < Bs[o.second]; ++b) items.push_back(make_int2(o.second, b));
+    CUDA_TRY(cudaStreamSynchronize(s));  // earlier launches may still read the old list
+    if (items.size() > bt->items_cap) {
+        if (bt->d_items) CUDA_TRY(cudaFree(bt->d_items));
+        bt->d_items = nullptr;
+        bt->items_cap = 0;
+        CUDA_TRY(cudaMalloc(&bt->d_items, std::max<size_t>(items.size(), 1) * sizeof(int2)));
+        bt->items_cap = std::max<size_t>(items.size(), 1);
+    }
+    if (!items.empty())
+        CUDA_TRY(cudaMemcpyAsync(bt->d_items, items.data(), items.size() * sizeof(int2), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));  // items is a host temporary
+    bt->n_items = (int)items.size();
+    bt->items_B = Bs;
+    return FFSAT_OK;
+}
+
+int batch_launch(ffsat_batch *bt, const ffsat_batch_io *io, int32_t dtype, int mode, const ffsat_step_args *args,
+                 cudaStream_t s) {
+    const bool f64 = dtype == FFSAT_F64;
+    const int K = (int)bt->insts.size();
+    const size_t elem = f64 ? sizeof(double) : sizeof(float);
+    for (int k = 0; k < K; ++k) {
+        if (io[k].B < 0) return fail(FFSAT_ERR_ARG, "io[%d].B must be >= 0", k);
+        if (io[k].B > 0 && !io[k].x) return fail(FFSAT_ERR_ARG, "io[%d].x is NULL", k);
+    }
+    // gradient scratch for step on instances without the gradient in shared memory
+    size_t need = 0;
+    std::vector<size_t> scr_off(K, 0);
+    if (mode == MODE_STEP) {
+        for (int k = 0; k < K; ++k) {
+            const int m = f64 ? bt->insts[k]->smem_mode64 : bt->insts[k]->smem_mode32;
+            if (m == SMEM_X || m == SMEM_NONE) {
+                scr_off[k] = need;
+                need += ((size_t)io[k].B * (size_t)bt->insts[k]->n * elem + 255) & ~size_t(255);
+            }
+        }
+        if (need > bt->scratch_bytes) {
+            if (bt->d_scratch) CUDA_TRY(cudaFree(bt->d_scratch));
+            bt->d_scratch = nullptr;
+            bt->scratch_bytes = 0;
+            CUDA_TRY(cudaMalloc(&bt->d_scratch, need));
+            bt->scratch_bytes = need;
+        }
+    }
+    int rc = batch_items(bt, io, s);
+    if (rc) return rc;
+    if (bt->n_items == 0) return FFSAT_OK;
+    // per-instance table (views, buffers, shared-memory modes); step parameters go
+    // by value so that a loop over fixed buffers enqueues only a memset and a launch
+    std::vector<BatchInst> tab(K);
+    std::memset(tab.data(), 0, tab.size() * sizeof(BatchInst));
+    for (int k = 0; k < K; ++k) {
+        ffsat_instance *I = bt->insts[k];
+        BatchInst &bi = tab[k];
+        bi.V = f64 ? I->V64 : I->V32;
+        bi.mode = f64 ? I->smem_mode64 : I->smem_mode32;
+        FusedArgs &a = bi.A;
+        a.B = io[k].B;
+        a.mode = mode;
+        a.x_in = io[k].x;
+        if (mode == MODE_STEP) {
+            a.x_out = io[k].x;
+            a.solved = io[k].solved;
+            a.n_unsat = io[k].n_unsat;
+            a.sp.b_offset = io[k].b_offset;
+            if (bi.mode == SMEM_X || bi.mode == SMEM_NONE)
+                a.g_scratch = static_cast<unsigned char *>(bt->d_scratch) + scr_off[k];
+        } else {
+            a.f = io[k].f;
+            a.g = io[k].g;
+        }
+    }
+    if (bt->h_insts_dtype != dtype || bt->h_insts.size() != tab.size() ||
+        std::memcmp(bt->h_insts.data(), tab.data(), tab.size() * sizeof(BatchInst)) != 0) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        CUDA_TRY(cudaMemcpy(bt->d_insts, tab.data(), tab.size() * sizeof(BatchInst), cudaMemcpyHostToDevice));
+        bt->h_insts.swap(tab);
+        bt->h_insts_dtype = dtype;
+    }
+    StepParams sp{};
+    if (mode == MODE_STEP) {
+        sp.T = args->T;
+        sp.restart = args->restart;
+        sp.lr = args->lr;
+        sp.seed = args->seed;
+        sp.epoch = args->epoch;
+    }
+    CUDA_TRY(cudaMemsetAsync(bt->d_counter, 0, sizeof(int), s));
+    const int v = f64 ? 1 : 0;
+    CUDA_TRY(launch_batch(f64, bt->node_r[v], bt->d_insts, bt->d_items, bt->n_items, bt->d_counter, sp, bt->smem[v],
+                          bt->grid[v], s, false, nullptr));
+    t_launches = 1;
+    return FFSAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ffsat_batch_create(ffsat_instance *const *insts, int32_t count, ffsat_batch **out) {
+    t_err.clear();
+    if (!out || !insts || count <= 0) return fail(FFSAT_ERR_ARG, "insts, count > 0 and out are required");
+    *out = nullptr;
+    std::unique_ptr<ffsat_batch> bt(new ffsat_batch());
+    for (int k = 0; k < count; ++k) {
+        if (!insts[k]) return fail(FFSAT_ERR_ARG, "insts[%d] is NULL", k);
+        if (insts[k]->device != insts[0]->device) return fail(FFSAT_ERR_ARG, "instances live on different devices");
+        bt->insts.push_back(insts[k]);
+    }
+    bt->device = insts[0]->device;
+    bt->num_sms = insts[0]->num_sms;
+    CUDA_TRY(cudaSetDevice(bt->device));
+    for (int v = 0; v < 2; ++v) {
+        size_t smem = 0;
+        int nr = 0;
+        for (ffsat_instance *I : bt->insts) {
+            smem = std::max(smem, v ? I->smem64 : I->smem32);
+            if ((v ? I->nr64 : I->nr32) > 0) nr = 16;
+        }
+        bt->smem[v] = smem;
+        bt->node_r[v] = nr;
+        int per_sm = 0;
+        const StepParams none{};
+        CUDA_TRY(launch_batch(v == 1, nr, nullptr, nullptr, 0, nullptr, none, smem, 0, 0, true, &per_sm));
+        bt->grid[v] = std::max(1, per_sm) * bt->num_sms;
+    }
+    CUDA_TRY(cudaMalloc(&bt->d_insts, (size_t)count * sizeof(BatchInst)));
+    CUDA_TRY(cudaMalloc(&bt->d_counter, sizeof(int)));
+    *out = bt.release();
+    return FFSAT_OK;
+}
+
+int ffsat_batch_eval_grad(ffsat_batch *bt, const ffsat_batch_io *io, int32_t dtype, void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!bt || !io) return fail(FFSAT_ERR_ARG, "NULL argument");
+    int rc = check_dtype(dtype);
+    if (rc) return rc;
+    CUDA_TRY(cudaSetDevice(bt->device));
+    return batch_launch(bt, io, dtype, MODE_EVAL, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+int ffsat_batch_step(ffsat_batch *bt, const ffsat_batch_io *io, int32_t dtype, const ffsat_step_args *args,
+                     void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!bt || !io || !args) return fail(FFSAT_ERR_ARG, "NULL argument");
+    if (args->T < 0) return fail(FFSAT_ERR_ARG, "T must be >= 0");
+    if (!std::isfinite(args->lr)) return fail(FFSAT_ERR_ARG, "lr must be finite");
+    int rc = check_dtype(dtype);
+    if (rc) return rc;
+    CUDA_TRY(cudaSetDevice(bt->device));
+    return batch_launch(bt, io, dtype, MODE_STEP, args, static_cast<cudaStream_t>(stream));
+}
+
+void ffsat_batch_free(ffsat_batch *bt) {
+    if (!bt) return;
+    cudaSetDevice(bt->device);
+    if (bt->d_insts) cudaFree(bt->d_insts);
+    if (bt->d_counter) cudaFree(bt->d_counter);
+    if (bt->d_items) cudaFree(bt->d_items);
+    if (bt->d_scratch) cudaFree(bt->d_scratch);
+    delete bt;
 }
 
 int ffsat_sync_status(ffsat_instance *I, void *stream) {

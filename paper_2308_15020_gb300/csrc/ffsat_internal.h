@@ -105,6 +105,22 @@ struct FusedArgs {
     int32_t *n_unsat;
 };
 
+// One instance of a batch launch.
+struct BatchInst {
+    DevView V;
+    FusedArgs A;
+    int32_t mode;  // shared-memory mode of the instance for the launch's real type
+    int32_t pad[3];
+};
+
+// Batch-kernel launchers (f64: real type; node_r: 0 or 16).  With prepare_only
+// the launcher raises the dynamic shared-memory limit to `smem` and reports
+// through *blocks_per_sm how many CTAs of the kernel fit on one SM.
+cudaError_t launch_batch(bool f64, int node_r, const BatchInst *insts, const int2 *items, int n_items, int *counter,
+                         const StepParams &sp, size_t smem, int grid, cudaStream_t s, bool prepare_only,
+                         int *blocks_per_sm);
+int batch_threads(bool f64, int node_r);
+
 // Fused-kernel launchers, one per (real type, node R); each handles the three
 // shared-memory modes.  With prepare_only the launcher only raises the kernel's
 // dynamic shared-memory limit to `smem`.

@@ -238,7 +238,7 @@ __device__ __forceinline__ void prod_task(const DevView &V, const Src &S, int4 t
                                           const Acc &acc, bool want_g, R &facc) {
     constexpr int RL = kProdR;
     const int n = V.n;
-    const int G = task.x >> 8;
+    const int G = (task.x >> 8) & 0xff;
     const int seg = lane >> (__ffs(G) - 1);
     const int sl = lane & (G - 1);
     const int c = task.y + seg;
@@ -286,13 +286,14 @@ __device__ __forceinline__ void prod_task(const DevView &V, const Src &S, int4 t
 
 // ---------------------------------------------------------------------------
 // node path (DFT evaluation), NR literals per lane, G lanes per constraint,
-// NI nodes per iteration
+// NI nodes per iteration; SF: keep the factors of a node in registers between
+// the suffix and the prefix pass (else recompute them)
 // ---------------------------------------------------------------------------
-template <typename R, int NR, int NI, int XG, typename Acc>
+template <typename R, int NR, int NI, bool SF, int XG, typename Acc>
 __device__ __forceinline__ void node_task(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
                                           const Acc &acc, bool want_g, R &facc) {
     const int n = V.n;
-    const int G = task.x >> 8;
+    const int G = (task.x >> 8) & 0xff;
     const int seg = lane >> (__ffs(G) - 1);
     const int sl = lane & (G - 1);
     const int c = task.y + seg;
@@ -329,6 +330,21 @@ __device__ __forceinline__ void node_task(const DevView &V, const Src &S, int4 t
         Node<R> nx[NI];
 #pragma unroll
         for (int q = 0; q < NI; ++q) nx[q] = (j0 + NI + q < Jc) ? load_node(V, R(0), toff + j0 + NI + q) : zero;
+        // factors f_r = alpha_j + beta_j y_r (Eq. forward)
+        C2<R> fac[NI][SF ? NR : 1];
+        if constexpr (SF) {
+#pragma unroll
+            for (int r = 0; r < NR; ++r)
+#pragma unroll
+                for (int q = 0; q < NI; ++q)
+                    fac[q][r] = {nd[q].a.re + nd[q].b.re * y[r], nd[q].a.im + nd[q].b.im * y[r]};
+        }
+        auto factor = [&](int q, int r) -> C2<R> {
+            if constexpr (SF)
+                return fac[q][r];
+            else
+                return {nd[q].a.re + nd[q].b.re * y[r], nd[q].a.im + nd[q].b.im * y[r]};
+        };
         // in-lane suffix products suf[r] = prod_{k > r} f_k
         C2<R> suf[NI][NR];
 #pragma unroll
@@ -336,17 +352,13 @@ __device__ __forceinline__ void node_task(const DevView &V, const Src &S, int4 t
 #pragma unroll
         for (int r = NR - 1; r >= 1; --r) {
 #pragma unroll
-            for (int q = 0; q < NI; ++q) {
-                const C2<R> f = {nd[q].a.re + nd[q].b.re * y[r], nd[q].a.im + nd[q].b.im * y[r]};
-                suf[q][r - 1] = cmul(suf[q][r], f);
-            }
+            for (int q = 0; q < NI; ++q) suf[q][r - 1] = cmul(suf[q][r], factor(q, r));
         }
         C2<R> P[NI], X[NI];
 #pragma unroll
         for (int q = 0; q < NI; ++q) {
-            const C2<R> f0 = {nd[q].a.re + nd[q].b.re * y[0], nd[q].a.im + nd[q].b.im * y[0]};
-            P[q] = cmul(f0, suf[q][0]);  // this lane's product
-            X[q] = {R(1), R(0)};         // product of the other lanes of the segment
+            P[q] = cmul(factor(q, 0), suf[q][0]);  // this lane's product
+            X[q] = {R(1), R(0)};                   // product of the other lanes of the segment
         }
         for (int s = 1; s < G; s <<= 1) {
 #pragma unroll
@@ -368,10 +380,7 @@ __device__ __forceinline__ void node_task(const DevView &V, const Src &S, int4 t
 #pragma unroll
             for (int q = 0; q < NI; ++q) {
                 gacc[r] += pre[q].re * suf[q][r].re - pre[q].im * suf[q][r].im;
-                if (r + 1 < NR) {
-                    const C2<R> f = {nd[q].a.re + nd[q].b.re * y[r], nd[q].a.im + nd[q].b.im * y[r]};
-                    pre[q] = cmul(pre[q], f);
-                }
+                if (r + 1 < NR) pre[q] = cmul(pre[q], factor(q, r));
             }
         }
 #pragma unroll
@@ -451,17 +460,61 @@ __device__ __forceinline__ R restart_value(uint64_t key_b, uint64_t v) {
 }
 
 // ---------------------------------------------------------------------------
-// the fused kernel
+// the per-point body (shared by the single-instance and the batch kernels)
 // ---------------------------------------------------------------------------
+// Shared-memory layout: x | gradient words | resident image (SMEM_RES); the
+// image part is set up by the caller (make_src).
+template <typename R, int SM>
+__device__ __forceinline__ size_t image_offset(int n) {
+    const int npad = (n + 2 + 3) & ~3;
+    constexpr bool FIX = SM == SMEM_RES && sizeof(R) == 4;
+    return FIX ? 4 * (size_t)npad * 4 : 2 * (size_t)npad * sizeof(R);
+}
+
+// Constraint-data view for the point loop; SMEM_RES copies the image into shared
+// memory first (skipped when copy is false: the same instance's image is there).
+template <typename R, int SM, int THREADS>
+__device__ __forceinline__ Src make_src(const DevView &V, unsigned char *smem_raw, bool copy) {
+    Src S;
+    if constexpr (SM == SMEM_RES) {
+        int4 *img = reinterpret_cast<int4 *>(smem_raw + image_offset<R, SM>(V.n));
+        if (copy)
+            for (int i = threadIdx.x; i < V.res_int4; i += THREADS) img[i] = __ldg(&V.res_image[i]);
+        S.tasks = img + V.res_off_tasks;
+        S.clauses = img + V.res_off_clauses;
+        S.segmeta = img + V.res_off_segmeta;
+        S.seg_lits = reinterpret_cast<const int32_t *>(img + V.res_off_lits);
+    } else {
+        S.tasks = V.tasks;
+        S.clauses = V.clauses;
+        S.segmeta = V.segmeta;
+        S.seg_lits = V.seg_lits;
+    }
+    return S;
+}
+
+struct BlockShared {
+    int ctr;
+    double red[32];
+    int ired[32];
+};
+
+// One point b of one instance: stage x, T projected-GD iterations (or one
+// evaluation), exact check and restart.  All threads of the CTA take part.
 template <typename R, int NR, int NI, int SM, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1) fused_kernel(const DevView V, const FusedArgs A) {
+__device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, int b, unsigned char *smem_raw,
+                                          const Src &S, BlockShared &sh) {
+    constexpr bool SF = sizeof(R) == 4;  // FP32 keeps node factors in registers
     // SMEM_RES keeps x and g in shared memory like SMEM_FULL and adds the resident image.
     constexpr bool RES = SM == SMEM_RES;
     constexpr int XG = RES ? SMEM_FULL : SM;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int s_ctr;
-    __shared__ double s_red[32];
-    __shared__ int s_ired[32];
+    // FP32 shared-resident mode: x | g hi words | g lo words | g FP32 words | image;
+    // otherwise x | g | image.
+    constexpr bool FIX = RES && sizeof(R) == 4;
+    using Acc = typename std::conditional<FIX, FixAcc, PlainAcc<R>>::type;
+    int &s_ctr = sh.ctr;
+    double *s_red = sh.red;
+    int *s_ired = sh.ired;
 
     const int n = V.n;
     const int npad = (n + 2 + 3) & ~3;  // n variables + 2 dummies, rounded to 4
@@ -475,142 +528,190 @@ __global__ void __launch_bounds__(THREADS, 1) fused_kernel(const DevView V, cons
     R *g_scr = static_cast<R *>(A.g_scratch);
     const R lr = R(A.sp.lr);
 
-    // FP32 shared-resident mode: x | g hi words | g lo words | g FP32 words | image;
-    // otherwise x | g | image.
-    constexpr bool FIX = RES && sizeof(R) == 4;
-    using Acc = typename std::conditional<FIX, FixAcc, PlainAcc<R>>::type;
-    const size_t img_off = FIX ? 4 * (size_t)npad * 4 : 2 * (size_t)npad * sizeof(R);
-
-    Src S;
-    if constexpr (RES) {
-        int4 *img = reinterpret_cast<int4 *>(smem_raw + img_off);
-        for (int i = tid; i < V.res_int4; i += THREADS) img[i] = __ldg(&V.res_image[i]);
-        S.tasks = img + V.res_off_tasks;
-        S.clauses = img + V.res_off_clauses;
-        S.segmeta = img + V.res_off_segmeta;
-        S.seg_lits = reinterpret_cast<const int32_t *>(img + V.res_off_lits);
+    const size_t rowoff = (size_t)b * (size_t)n;
+    // ---- stage x ----
+    const R *xrow;
+    if constexpr (XG != SMEM_NONE) {
+        bool bad = false;
+        for (int v = tid; v < n; v += THREADS) {
+            const R xv = x_in[rowoff + v];
+            bad |= isnan(xv);
+            xs[v] = xv;
+        }
+        if (tid == 0) {
+            xs[n] = R(1);
+            xs[n + 1] = R(0);
+        }
+        if (bad) atomicOr(V.status, STATUS_NAN);
+        xrow = xs;
     } else {
-        S.tasks = V.tasks;
-        S.clauses = V.clauses;
-        S.segmeta = V.segmeta;
-        S.seg_lits = V.seg_lits;
+        if (step && x_out != x_in) {
+            for (int v = tid; v < n; v += THREADS) x_out[rowoff + v] = x_in[rowoff + v];
+            __syncthreads();
+        }
+        xrow = step ? x_out + rowoff : x_in + rowoff;
+        bool bad = false;
+        for (int v = tid; v < n; v += THREADS) bad |= isnan(xrow[v]);
+        if (bad) atomicOr(V.status, STATUS_NAN);
     }
+    Acc G;
+    bool want_g;
+    int glen;
+    if constexpr (FIX) {
+        G.hi = reinterpret_cast<int *>(smem_raw + (size_t)npad * 4);
+        G.lo = G.hi + npad;
+        G.gf = reinterpret_cast<float *>(G.lo + npad);
+        G.s1 = V.fix_s1;
+        G.s2 = V.fix_s2;
+        G.i1 = V.fix_i1;
+        G.i12 = V.fix_i12;
+        want_g = step || g_out != nullptr;
+        glen = npad;
+    } else if constexpr (XG == SMEM_FULL) {
+        G.g = gs;
+        want_g = step || g_out != nullptr;
+        glen = npad;
+    } else {
+        G.g = step ? g_scr + rowoff : (g_out ? g_out + rowoff : nullptr);
+        want_g = G.g != nullptr;
+        glen = n;
+    }
+    if (want_g)
+        for (int v = tid; v < glen; v += THREADS) G.zero(v);
 
-    for (int b = blockIdx.x; b < A.B; b += gridDim.x) {
-        const size_t rowoff = (size_t)b * (size_t)n;
-        // ---- stage x ----
-        const R *xrow;
-        if constexpr (XG != SMEM_NONE) {
-            bool bad = false;
-            for (int v = tid; v < n; v += THREADS) {
-                const R xv = x_in[rowoff + v];
-                bad |= isnan(xv);
-                xs[v] = xv;
-            }
-            if (tid == 0) {
-                xs[n] = R(1);
-                xs[n + 1] = R(0);
-            }
-            if (bad) atomicOr(V.status, STATUS_NAN);
-            xrow = xs;
-        } else {
-            if (step && x_out != x_in) {
-                for (int v = tid; v < n; v += THREADS) x_out[rowoff + v] = x_in[rowoff + v];
-                __syncthreads();
-            }
-            xrow = step ? x_out + rowoff : x_in + rowoff;
-            bool bad = false;
-            for (int v = tid; v < n; v += THREADS) bad |= isnan(xrow[v]);
-            if (bad) atomicOr(V.status, STATUS_NAN);
-        }
-        Acc G;
-        bool want_g;
-        int glen;
-        if constexpr (FIX) {
-            G.hi = reinterpret_cast<int *>(smem_raw + (size_t)npad * 4);
-            G.lo = G.hi + npad;
-            G.gf = reinterpret_cast<float *>(G.lo + npad);
-            G.s1 = V.fix_s1;
-            G.s2 = V.fix_s2;
-            G.i1 = V.fix_i1;
-            G.i12 = V.fix_i12;
-            want_g = step || g_out != nullptr;
-            glen = npad;
-        } else if constexpr (XG == SMEM_FULL) {
-            G.g = gs;
-            want_g = step || g_out != nullptr;
-            glen = npad;
-        } else {
-            G.g = step ? g_scr + rowoff : (g_out ? g_out + rowoff : nullptr);
-            want_g = G.g != nullptr;
-            glen = n;
-        }
-        if (want_g)
-            for (int v = tid; v < glen; v += THREADS) G.zero(v);
-
-        const int iters = step ? A.sp.T : 1;
-        for (int it = 0; it < iters; ++it) {
-            if (tid == 0) s_ctr = 0;
-            __syncthreads();
-            R facc = R(0);
-            for (;;) {
-                int t = 0;
-                if (lane == 0) t = atomicAdd(&s_ctr, 1);
-                t = __shfl_sync(kFull, t, 0);
-                if (t >= V.n_task) break;
-                const int4 task = S.tasks[t];
-                const int kind = task.x & 0xff;
-                if (kind == TASK_CLAUSE) {
-                    clause_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
-                } else if (kind == TASK_PROD) {
-                    prod_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
-                } else {
-                    if constexpr (NR > 0) node_task<R, NR, NI, XG>(V, S, task, lane, xrow, G, want_g, facc);
-                }
-            }
-            __syncthreads();
-            if (!step) {
-                if (A.f) {
-                    const double tot = block_sum((double)facc, s_red);
-                    if (tid == 0) A.f[b] = tot + V.f_const_d;
-                }
-                if constexpr (XG == SMEM_FULL) {
-                    if (g_out)
-                        for (int v = tid; v < n; v += THREADS) g_out[rowoff + v] = G.get(v);
-                }
+    const int iters = step ? A.sp.T : 1;
+    for (int it = 0; it < iters; ++it) {
+        if (tid == 0) s_ctr = 0;
+        __syncthreads();
+        R facc = R(0);
+        for (;;) {
+            int t = 0;
+            if (lane == 0) t = atomicAdd(&s_ctr, 1);
+            t = __shfl_sync(kFull, t, 0);
+            if (t >= V.n_task) break;
+            const int4 task = S.tasks[t];
+            const int kind = task.x & 0xff;
+            if (kind == TASK_CLAUSE) {
+                clause_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
+            } else if (kind == TASK_PROD) {
+                prod_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
             } else {
-                // projected gradient step x <- clip(x - lr g, -1, 1); reset the accumulator
-                R *xw = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
-                for (int v = tid; v < n; v += THREADS) {
-                    R z = xw[v] - lr * G.get(v);
-                    z = z < R(-1) ? R(-1) : (z > R(1) ? R(1) : z);
-                    xw[v] = z;
-                    G.zero(v);
+                // node tasks carry their literals per lane in bits 16..23
+                const int nr = (task.x >> 16) & 0xff;
+                if constexpr (NR >= 16) {
+                    if (nr == 12)
+                        node_task<R, 12, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
+                    else
+                        node_task<R, 16, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
+                } else if constexpr (NR > 0) {
+                    node_task<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
                 }
-                __syncthreads();
-            }
-        }
-        if (step) {
-            const R *xc = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
-            const int unsat = block_unsat<R>(V, xc, s_ired);
-            if (tid == 0) s_ired[0] = unsat;
-            __syncthreads();
-            const int u = s_ired[0];
-            if (tid == 0) {
-                if (A.solved) A.solved[b] = (uint8_t)(u == 0);
-                if (A.n_unsat) A.n_unsat[b] = u;
-            }
-            R *xw = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
-            if (u != 0 && A.sp.restart) {
-                const uint64_t kb =
-                    splitmix64(splitmix64(splitmix64(A.sp.seed) ^ A.sp.epoch) ^ (A.sp.b_offset + (uint64_t)b));
-                for (int v = tid; v < n; v += THREADS) xw[v] = restart_value<R>(kb, (uint64_t)v);
-            }
-            if constexpr (XG != SMEM_NONE) {
-                for (int v = tid; v < n; v += THREADS) x_out[rowoff + v] = xs[v];
             }
         }
         __syncthreads();
+        if (!step) {
+            if (A.f) {
+                const double tot = block_sum((double)facc, s_red);
+                if (tid == 0) A.f[b] = tot + V.f_const_d;
+            }
+            if constexpr (XG == SMEM_FULL) {
+                if (g_out)
+                    for (int v = tid; v < n; v += THREADS) g_out[rowoff + v] = G.get(v);
+            }
+        } else {
+            // projected gradient step x <- clip(x - lr g, -1, 1); reset the accumulator
+            R *xw = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
+            for (int v = tid; v < n; v += THREADS) {
+                R z = xw[v] - lr * G.get(v);
+                z = z < R(-1) ? R(-1) : (z > R(1) ? R(1) : z);
+                xw[v] = z;
+                G.zero(v);
+            }
+            __syncthreads();
+        }
+    }
+    if (step) {
+        const R *xc = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
+        const int unsat = block_unsat<R>(V, xc, s_ired);
+        if (tid == 0) s_ired[0] = unsat;
+        __syncthreads();
+        const int u = s_ired[0];
+        if (tid == 0) {
+            if (A.solved) A.solved[b] = (uint8_t)(u == 0);
+            if (A.n_unsat) A.n_unsat[b] = u;
+        }
+        R *xw = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
+        if (u != 0 && A.sp.restart) {
+            const uint64_t kb =
+                splitmix64(splitmix64(splitmix64(A.sp.seed) ^ A.sp.epoch) ^ (A.sp.b_offset + (uint64_t)b));
+            for (int v = tid; v < n; v += THREADS) xw[v] = restart_value<R>(kb, (uint64_t)v);
+        }
+        if constexpr (XG != SMEM_NONE) {
+            for (int v = tid; v < n; v += THREADS) x_out[rowoff + v] = xs[v];
+        }
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// the fused kernel: one instance, points b = blockIdx.x, blockIdx.x + gridDim.x, ...
+// ---------------------------------------------------------------------------
+template <typename R, int NR, int NI, int SM, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) fused_kernel(const DevView V, const FusedArgs A) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockShared sh;
+    const Src S = make_src<R, SM, THREADS>(V, smem_raw, true);
+    for (int b = blockIdx.x; b < A.B; b += gridDim.x) run_point<R, NR, NI, SM, THREADS>(V, A, b, smem_raw, S, sh);
+}
+
+// ---------------------------------------------------------------------------
+// the batch kernel: several instances of uneven size in one persistent launch.
+// Each CTA pulls (instance, point) items, ordered by decreasing estimated cost,
+// from a global counter; no CTA ever waits on another.
+// ---------------------------------------------------------------------------
+template <typename R, int NR, int NI, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) batch_kernel(const BatchInst *__restrict__ insts,
+                                                           const int2 *__restrict__ items, int n_items,
+                                                           int *counter, const StepParams sp) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockShared sh;
+    __shared__ int s_item;
+    int cur = -1;  // instance whose resident image is in shared memory
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_items) break;
+        const int2 item = items[it];
+        const BatchInst &BI = insts[item.x];
+        // the call's step parameters; the restart key offset stays per instance
+        FusedArgs A = BI.A;
+        const uint64_t b_offset = A.sp.b_offset;
+        A.sp = sp;
+        A.sp.b_offset = b_offset;
+        switch (BI.mode) {
+        case SMEM_RES: {
+            const Src S = make_src<R, SMEM_RES, THREADS>(BI.V, smem_raw, item.x != cur);
+            cur = item.x;
+            run_point<R, NR, NI, SMEM_RES, THREADS>(BI.V, A, item.y, smem_raw, S, sh);
+            break;
+        }
+        case SMEM_FULL:
+            cur = -1;
+            run_point<R, NR, NI, SMEM_FULL, THREADS>(BI.V, A, item.y, smem_raw,
+                                                     make_src<R, SMEM_FULL, THREADS>(BI.V, smem_raw, false), sh);
+            break;
+        case SMEM_X:
+            cur = -1;
+            run_point<R, NR, NI, SMEM_X, THREADS>(BI.V, A, item.y, smem_raw,
+                                                  make_src<R, SMEM_X, THREADS>(BI.V, smem_raw, false), sh);
+            break;
+        default:
+            cur = -1;
+            run_point<R, NR, NI, SMEM_NONE, THREADS>(BI.V, A, item.y, smem_raw,
+                                                     make_src<R, SMEM_NONE, THREADS>(BI.V, smem_raw, false), sh);
+        }
     }
 }
 

@@ -1,15 +1,42 @@
 // Launcher body shared by the per-variant translation units.
 #pragma once
+#include <map>
+#include <mutex>
+
 #include "fused_kernel.cuh"
 
 namespace ffsat {
 namespace dev {
 
-// Nodes per iteration of the node loop: two independent multiply chains in
-// FP32, one in FP64 (register budget).
+// Raise a kernel's dynamic shared-memory limit to at least `smem`.  The limit
+// belongs to the kernel, not to an instance, so it only ever grows: a later,
+// smaller instance must not lower it below what an earlier one launches with.
+inline std::mutex &smem_limit_mutex() {
+    static std::mutex mu;
+    return mu;
+}
+inline std::map<const void *, size_t> &smem_limits() {
+    static std::map<const void *, size_t> limits;
+    return limits;
+}
+
+template <typename Kernel>
+cudaError_t raise_smem_limit(Kernel k, size_t smem) {
+    std::lock_guard<std::mutex> lock(smem_limit_mutex());
+    size_t &current = smem_limits()[reinterpret_cast<const void *>(k)];
+    if (current == 0) current = 48 * 1024;
+    if (smem <= current) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) current = smem;
+    return e;
+}
+
+// Nodes per iteration of the node loop (independent multiply chains): one.
+// FP32 keeps the node factors in registers instead, which leaves no register
+// budget for a second chain at 16 literals per lane.
 template <typename R, int NR>
 constexpr int node_interleave() {
-    return (sizeof(R) == 4 && NR > 0) ? 2 : 1;
+    return 1;
 }
 
 template <typename R, int NR, int SM>
@@ -17,7 +44,7 @@ cudaError_t fused_launch_mode(const DevView &V, const FusedArgs &a, size_t smem,
                               bool prepare_only) {
     constexpr int TH = fused_threads(sizeof(R) == 8, NR);
     auto k = fused_kernel<R, NR, node_interleave<R, NR>(), SM, TH>;
-    if (prepare_only) return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (prepare_only) return raise_smem_limit(k, smem);
     k<<<grid, TH, smem, s>>>(V, a);
     return cudaGetLastError();
 }

@@ -47,6 +47,10 @@ SYMBOLS = (
     "ffsat_step",
     "ffsat_step_noalloc",
     "ffsat_check",
+    "ffsat_batch_create",
+    "ffsat_batch_eval_grad",
+    "ffsat_batch_step",
+    "ffsat_batch_free",
     "ffsat_sync_status",
     "ffsat_instance_info",
     "ffsat_last_launch_count",
@@ -71,15 +75,22 @@ class StepArgs(C.Structure):
                 ("epoch", C.c_uint64), ("b_offset", C.c_uint64)]
 
 
+class BatchIO(C.Structure):
+    _fields_ = [("B", C.c_int32), ("pad", C.c_int32), ("x", C.c_void_p), ("f", C.c_void_p), ("g", C.c_void_p),
+                ("solved", C.c_void_p), ("n_unsat", C.c_void_p), ("b_offset", C.c_uint64)]
+
+
 class Info(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int32), ("nnz", C.c_int64), ("n_clause3", C.c_int32),
                 ("n_product", C.c_int32), ("n_node", C.c_int32), ("n_const", C.c_int32), ("n_tables", C.c_int32),
                 ("n_tasks", C.c_int32), ("node_r", C.c_int32), ("smem_mode_f32", C.c_int32),
                 ("smem_mode_f64", C.c_int32), ("threads_f32", C.c_int32), ("node_lane_work", C.c_int64),
-                ("device_bytes", C.c_int64)]
+                ("device_bytes", C.c_int64), ("autotuned", C.c_int32), ("autotune_us", C.c_float * 2)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["autotune_us"] = list(self.autotune_us)
+        return d
 
 
 _lib = None
@@ -112,6 +123,14 @@ def lib():
         L.ffsat_step_noalloc.restype = C.c_int
         L.ffsat_check.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
         L.ffsat_check.restype = C.c_int
+        L.ffsat_batch_create.argtypes = [C.POINTER(_vp), C.c_int32, C.POINTER(_vp)]
+        L.ffsat_batch_create.restype = C.c_int
+        L.ffsat_batch_eval_grad.argtypes = [_vp, C.POINTER(BatchIO), C.c_int32, _vp]
+        L.ffsat_batch_eval_grad.restype = C.c_int
+        L.ffsat_batch_step.argtypes = [_vp, C.POINTER(BatchIO), C.c_int32, C.POINTER(StepArgs), _vp]
+        L.ffsat_batch_step.restype = C.c_int
+        L.ffsat_batch_free.argtypes = [_vp]
+        L.ffsat_batch_free.restype = None
         L.ffsat_sync_status.argtypes = [_vp, _vp]
         L.ffsat_sync_status.restype = C.c_int
         L.ffsat_instance_info.argtypes = [_vp, C.POINTER(Info)]
@@ -285,6 +304,70 @@ class Instance:
 
     def sync_status(self, stream=None):
         _check(lib().ffsat_sync_status(self.handle, _stream(stream)))
+
+
+class Batch:
+    """Several loaded instances evaluated in one launch (``ffsat_batch_*``)."""
+
+    def __init__(self, instances):
+        self.instances = list(instances)  # keep them alive
+        arr = (_vp * len(self.instances))(*[h.handle for h in self.instances])
+        h = _vp()
+        _check(lib().ffsat_batch_create(arr, len(self.instances), C.byref(h)))
+        self.handle = h.value
+
+    def free(self):
+        if getattr(self, "handle", None):
+            lib().ffsat_batch_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def _io(self, xs, fs=None, gs=None, solved=None, n_unsat=None, b_offsets=None):
+        io = (BatchIO * len(self.instances))()
+        dt = None
+        for k, x in enumerate(xs):
+            _need_cuda_contig(x, f"xs[{k}]")
+            d = _dtype_code(x)
+            if dt is not None and d != dt:
+                raise TypeError("all x must share one dtype")
+            dt = d
+            io[k].B = x.shape[0]
+            io[k].x = x.data_ptr()
+            io[k].f = _ptr(fs[k]) if fs else None
+            io[k].g = _ptr(gs[k]) if gs else None
+            io[k].solved = _ptr(solved[k]) if solved else None
+            io[k].n_unsat = _ptr(n_unsat[k]) if n_unsat else None
+            io[k].b_offset = int(b_offsets[k]) if b_offsets is not None else 0
+        return io, dt
+
+    def eval_grad(self, xs, fs=None, gs=None, stream=None):
+        import torch
+
+        if fs is None:
+            fs = [torch.empty(x.shape[0], dtype=torch.float64, device=x.device) for x in xs]
+        if gs is None:
+            gs = [torch.empty_like(x) for x in xs]
+        io, dt = self._io(xs, fs, gs)
+        _check(lib().ffsat_batch_eval_grad(self.handle, io, dt, _stream(stream)))
+        return fs, gs
+
+    def step(self, xs, T: int, lr: float, seed: int = 0, epoch: int = 0, restart: bool = True, b_offsets=None,
+             solved=None, n_unsat=None, stream=None):
+        import torch
+
+        if solved is None:
+            solved = [torch.empty(x.shape[0], dtype=torch.uint8, device=x.device) for x in xs]
+        if n_unsat is None:
+            n_unsat = [torch.empty(x.shape[0], dtype=torch.int32, device=x.device) for x in xs]
+        io, dt = self._io(xs, solved=solved, n_unsat=n_unsat, b_offsets=b_offsets)
+        a = StepArgs(int(T), int(restart), float(lr), int(seed) & (2**64 - 1), int(epoch), 0)
+        _check(lib().ffsat_batch_step(self.handle, io, dt, C.byref(a), _stream(stream)))
+        return solved, n_unsat
 
 
 def load_instance(inst, **kw) -> Instance:
