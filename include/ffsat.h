@@ -231,6 +231,52 @@ int ffsat_batch_step(ffsat_batch *bt, const ffsat_batch_io *io, int32_t dtype, c
 /* Release the batch (not its instances). */
 void ffsat_batch_free(ffsat_batch *bt);
 
+/* ---- learned restart proposal (no counterpart in the paper) -------------------------- */
+
+typedef struct ffsat_mpnn ffsat_mpnn;
+
+/* A message-passing network over the variable-constraint graph proposing restart
+ * points (hidden width H = 64, `layers` = L rounds):
+ *   h_v = relu(Wv0 f_v + bv0), h_c = relu(Wc0 f_c + bc0)
+ *   per round: m_c = mean_{v in c} s_cv (A h_v);  h_c = relu(Uc [h_c; m_c] + buc)
+ *              m_v = mean_{c ni v} s_cv (B h_c);  h_v = relu(Uv [h_v; m_v] + buv)
+ *   z_v = wo . h_v + bo, proposal x0_v = tanh(z_v);  s_cv = -1 for a negated literal.
+ * Variable features f_v (8): 1, positive and negative clause occurrences over the
+ * mean degree (nnz / n), (pos - neg) / (pos + neg + 1) over clause occurrences,
+ * XOR occurrences over the mean degree, (pos - neg) / (pos + neg + 1) over
+ * cardinality occurrences, total occurrences over the mean degree, 0.
+ * Constraint features f_c (8): 1, is OR, is XOR, is ATLEAST, length / 10, XOR
+ * parity as +1 (odd) / -1 (even) else 0, K / length for ATLEAST else 0, 0.
+ * Parameter vector (FP32, weights row-major [out x in]): Wv0 [64x8], bv0 [64],
+ * Wc0 [64x8], bc0 [64], then per round A [64x64], Uc [64x128], buc [64],
+ * B [64x64], Uv [64x128], buv [64], then wo [64], bo [1].
+ * Kernels use the weights as BF16 (FP32 master copy for Adam) with FP32
+ * activations and accumulation.  Initialisation: Glorot-uniform weights from
+ * splitmix64(seed), zero biases.  The network lives on the current device. */
+int ffsat_mpnn_create(int32_t layers, uint64_t seed, ffsat_mpnn **out);
+int32_t ffsat_mpnn_num_params(const ffsat_mpnn *net);
+/* Copy the FP32 master parameters to / from a HOST array of num_params floats. */
+int ffsat_mpnn_get_params(const ffsat_mpnn *net, float *host);
+int ffsat_mpnn_set_params(ffsat_mpnn *net, const float *host);
+/* x0 (device [n] float) = the proposal for the instance. */
+int ffsat_mpnn_forward(ffsat_mpnn *net, ffsat_instance *inst, float *x0, void *stream);
+/* Loss mean_v softplus(-t_v z_v) for sign targets t (device [n], values -1/+1)
+ * into *loss (device float), proposal into x0 (device [n] or NULL), and the
+ * parameter gradient (kept for ffsat_mpnn_adam_step; copied to grad_host, a HOST
+ * array of num_params floats, when not NULL — that copy synchronises). */
+int ffsat_mpnn_loss_grad(ffsat_mpnn *net, ffsat_instance *inst, const float *target, float *loss, float *x0,
+                         float *grad_host, void *stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) with the last gradient. */
+int ffsat_mpnn_adam_step(ffsat_mpnn *net, float lr, void *stream);
+/* Restart from a proposal: every point b with solved[b] == 0 (all points when
+ * solved is NULL) gets x_v = clip(proposal_v + noise * u, -1, 1), where u is the
+ * same counter-based uniform draw on [-1, 1) as the uniform restart of ffsat_step
+ * for (seed, epoch, b_offset + b, v). */
+int ffsat_restart_from_proposal(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, const float *proposal,
+                                float noise, const uint8_t *solved, uint64_t seed, uint64_t epoch, uint64_t b_offset,
+                                void *stream);
+void ffsat_mpnn_free(ffsat_mpnn *net);
+
 /* Synchronise `stream`, read and clear the instance's device status word:
  * FFSAT_OK, FFSAT_ERR_NAN or FFSAT_ERR_DEVICE. */
 int ffsat_sync_status(ffsat_instance *inst, void *stream);

@@ -540,6 +540,38 @@ int orc_check(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *lits,
     return status;
 }
 
+int orc_unsat_counts(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *lits,
+                     const uint8_t *type, const int32_t *param, int32_t B, const double *x, int32_t *U) {
+    for (int32_t c = 0; c < m; ++c) U[c] = 0;
+    for (int32_t b = 0; b < B; ++b) {
+        const double *xb = x + (size_t)b * n;
+        for (int32_t c = 0; c < m; ++c) {
+            int64_t a = row_ptr[c];
+            int L = (int)(row_ptr[c + 1] - a);
+            int s = 0;
+            for (int i = 0; i < L; ++i) {
+                int32_t lit = lits[a + i];
+                int32_t v = (lit > 0 ? lit : -lit) - 1;
+                if (v < 0 || v >= n || isnan(xb[v])) return -1;
+                int var_true = xb[v] < 0.0;
+                s += lit > 0 ? var_true : !var_true;
+            }
+            if (orc_value(type[c], param[c], L, s) > 0) U[c] += 1;
+        }
+    }
+    return 0;
+}
+
+void orc_erwa(int32_t m, const int32_t *U, double alpha, double *w) {
+    int32_t umax = 0;
+    for (int32_t c = 0; c < m; ++c)
+        if (U[c] > umax) umax = U[c];
+    for (int32_t c = 0; c < m; ++c) {
+        double r = umax > 0 ? (double)U[c] / (double)umax : 0.0;
+        w[c] = (1.0 - alpha) * w[c] + alpha * r;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Counter-based restart draws and one CLS round                            */
 /* ------------------------------------------------------------------------ */

@@ -106,6 +106,15 @@ int orc_check(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *lits,
               const uint8_t *type, const int32_t *param,
               int32_t B, const double *x, uint8_t *sat, int32_t *n_unsat, int nthreads);
 
+/* U[c] = number of the B points whose sign vector violates constraint c (the
+ * unsatisfaction count of the weighting heuristic, Sec. "Weighting Heuristics"). */
+int orc_unsat_counts(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *lits,
+                     const uint8_t *type, const int32_t *param, int32_t B, const double *x, int32_t *U);
+
+/* Prop. "Adaptive weight": r_c = U_c / max_c U_c (0 when every U_c is 0),
+ * w_c <- (1 - alpha) w_c + alpha r_c, in place. */
+void orc_erwa(int32_t m, const int32_t *U, double alpha, double *w);
+
 /* splitmix64 (Steele, Lea, Flood 2014): state += 0x9E3779B97F4A7C15, then the
  * published output mix.  Returns the output for the given pre-increment state. */
 uint64_t orc_splitmix64(uint64_t state);

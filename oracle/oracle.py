@@ -53,6 +53,10 @@ def lib():
         L.orc_eval_scale.restype = C.c_int
         L.orc_check.argtypes = [C.c_int32, C.c_int32, _i64, _i32, _u8, _i32, C.c_int32, _dp, _u8, _i32, C.c_int]
         L.orc_check.restype = C.c_int
+        L.orc_unsat_counts.argtypes = [C.c_int32, C.c_int32, _i64, _i32, _u8, _i32, C.c_int32, _dp, _i32]
+        L.orc_unsat_counts.restype = C.c_int
+        L.orc_erwa.argtypes = [C.c_int32, _i32, C.c_double, _dp]
+        L.orc_erwa.restype = None
         L.orc_splitmix64.argtypes = [C.c_uint64]
         L.orc_splitmix64.restype = C.c_uint64
         L.orc_uniform.argtypes = [C.c_uint64] * 4
@@ -209,6 +213,24 @@ def step(inst, x, T: int, lr: float, seed: int = 0, epoch: int = 0, b_offset: in
     if rc != 0:
         raise ValueError("oracle: bad input")
     return x, solved, nun
+
+
+def unsat_counts(inst, x):
+    rp, lits, ty, pa, _ = _inst_arrays(inst)
+    x = _f64(np.atleast_2d(x))
+    U = np.zeros(inst.m, dtype=np.int32)
+    rc = lib().orc_unsat_counts(inst.n, inst.m, _p(rp, _i64), _p(lits, _i32), _p(ty, _u8), _p(pa, _i32), x.shape[0],
+                                _p(x, _dp), _p(U, _i32))
+    if rc != 0:
+        raise ValueError("oracle: bad input")
+    return U
+
+
+def erwa(U, w, alpha: float = 0.4):
+    U = np.ascontiguousarray(U, dtype=np.int32)
+    w = _f64(w).copy()
+    lib().orc_erwa(len(w), _p(U, _i32), alpha, _p(w, _dp))
+    return w
 
 
 def splitmix64(state: int) -> int:

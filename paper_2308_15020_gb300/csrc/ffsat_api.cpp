@@ -168,6 +168,9 @@ struct ffsat_instance {
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
     ffsat_info info{};
+    // learned-proposal graph data (built on first use)
+    unsigned char *d_graph = nullptr;
+    GraphView graph{};
 };
 
 namespace {
@@ -1151,6 +1154,96 @@ int ffsat_check(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, uint
 
 }  // extern "C"
 
+namespace ffsat {
+
+// Variable features: 1, clause occurrences (positive, negative) over the mean
+// degree, their signed balance, XOR occurrences, the signed balance of
+// cardinality occurrences, the total degree over the mean, 0.  Constraint
+// features: 1, type one-hot (OR, XOR, ATLEAST), length / 10, XOR parity as
+// +-1, K / length, 0.
+int instance_graph(ffsat_instance *I, GraphView *out) {
+    if (I->d_graph) {
+        *out = I->graph;
+        return FFSAT_OK;
+    }
+    const int n = I->n, m = I->m;
+    std::vector<int32_t> var_ptr(n + 1, 0);
+    std::vector<float> pos(n, 0.f), neg(n, 0.f), nx(n, 0.f), cpos(n, 0.f), cneg(n, 0.f);
+    for (int64_t i = 0; i < I->nnz; ++i) {
+        const int32_t l = I->lits_in[i];
+        var_ptr[(l > 0 ? l : -l)] += 1;
+    }
+    for (int v = 0; v < n; ++v) var_ptr[v + 1] += var_ptr[v];
+    std::vector<uint32_t> occ((size_t)std::max<int64_t>(I->nnz, 1));
+    std::vector<int32_t> fill(var_ptr.begin(), var_ptr.end() - 1);
+    std::vector<float> fc((size_t)m * 8, 0.f), inv_len(std::max(m, 1), 0.f);
+    for (int32_t c = 0; c < m; ++c) {
+        const int64_t a = I->row_ptr[c], e = I->row_ptr[c + 1];
+        const int L = (int)(e - a);
+        const int t = I->type[c];
+        for (int64_t i = a; i < e; ++i) {
+            const int32_t l = I->lits_in[i];
+            const int32_t v = (l > 0 ? l : -l) - 1;
+            occ[fill[v]++] = (uint32_t)c | (l < 0 ? 0x80000000u : 0u);
+            if (t == FFSAT_OR) (l > 0 ? pos : neg)[v] += 1.f;
+            else if (t == FFSAT_XOR) nx[v] += 1.f;
+            else (l > 0 ? cpos : cneg)[v] += 1.f;
+        }
+        float *f = &fc[(size_t)c * 8];
+        f[0] = 1.f;
+        f[1] = t == FFSAT_OR;
+        f[2] = t == FFSAT_XOR;
+        f[3] = t == FFSAT_ATLEAST;
+        f[4] = (float)L / 10.f;
+        f[5] = t == FFSAT_XOR ? ((I->param[c] & 1) ? 1.f : -1.f) : 0.f;
+        f[6] = t == FFSAT_ATLEAST ? (float)I->param[c] / (float)L : 0.f;
+        inv_len[c] = 1.f / (float)L;
+    }
+    const float mean_deg = n > 0 ? (float)I->nnz / (float)n : 1.f;
+    std::vector<float> fv((size_t)n * 8, 0.f), inv_deg(std::max(n, 1), 0.f);
+    for (int v = 0; v < n; ++v) {
+        const float d = (float)(var_ptr[v + 1] - var_ptr[v]);
+        float *f = &fv[(size_t)v * 8];
+        f[0] = 1.f;
+        f[1] = pos[v] / mean_deg;
+        f[2] = neg[v] / mean_deg;
+        f[3] = (pos[v] - neg[v]) / (pos[v] + neg[v] + 1.f);
+        f[4] = nx[v] / mean_deg;
+        f[5] = (cpos[v] - cneg[v]) / (cpos[v] + cneg[v] + 1.f);
+        f[6] = d / mean_deg;
+        inv_deg[v] = d > 0 ? 1.f / d : 0.f;
+    }
+    std::vector<int32_t> rp32(m + 1);
+    for (int c = 0; c <= m; ++c) rp32[c] = (int32_t)I->row_ptr[c];
+    std::vector<uint32_t> lp((size_t)std::max<int64_t>(I->nnz, 1));
+    for (int64_t i = 0; i < I->nnz; ++i) lp[i] = (uint32_t)pack_lit(I->lits_in[i]);
+    Arena A;
+    const size_t o_rp = A.put(rp32), o_l = A.put(lp), o_vp = A.put(var_ptr), o_vo = A.put(occ), o_fv = A.put(fv),
+                 o_fc = A.put(fc), o_id = A.put(inv_deg), o_il = A.put(inv_len);
+    CUDA_TRY(cudaSetDevice(I->device));
+    CUDA_TRY(cudaMalloc(&I->d_graph, A.host.size()));
+    CUDA_TRY(cudaMemcpy(I->d_graph, A.host.data(), A.host.size(), cudaMemcpyHostToDevice));
+    GraphView &g = I->graph;
+    g.device = I->device;
+    g.n = n;
+    g.m = m;
+    g.row_ptr = reinterpret_cast<const int32_t *>(I->d_graph + o_rp);
+    g.lits = reinterpret_cast<const uint32_t *>(I->d_graph + o_l);
+    g.var_ptr = reinterpret_cast<const int32_t *>(I->d_graph + o_vp);
+    g.var_occ = reinterpret_cast<const uint32_t *>(I->d_graph + o_vo);
+    g.fv = reinterpret_cast<const float *>(I->d_graph + o_fv);
+    g.fc = reinterpret_cast<const float *>(I->d_graph + o_fc);
+    g.inv_deg = reinterpret_cast<const float *>(I->d_graph + o_id);
+    g.inv_len = reinterpret_cast<const float *>(I->d_graph + o_il);
+    *out = g;
+    return FFSAT_OK;
+}
+
+// ffsat_last_error for code outside this file.
+int set_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
+}  // namespace ffsat
+
 struct ffsat_batch {
     int device = 0;
     int num_sms = 0;
@@ -1376,6 +1469,7 @@ int ffsat_instance_info(const ffsat_instance *I, ffsat_info *info) {
 void ffsat_free(ffsat_instance *I) {
     if (!I) return;
     cudaSetDevice(I->device);
+    if (I->d_graph) cudaFree(I->d_graph);
     if (I->d_arena) cudaFree(I->d_arena);
     if (I->d_status) cudaFree(I->d_status);
     if (I->d_scratch) cudaFree(I->d_scratch);

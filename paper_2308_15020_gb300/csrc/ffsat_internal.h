@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+struct ffsat_instance;
+
 namespace ffsat {
 
 // Literals per lane on the product (closed-form) path.
@@ -137,6 +139,26 @@ FFSAT_FUSED_LAUNCHER(fused_f64_r16);
 // Device address of the statically reserved scratch (FFSAT_STATIC_SCRATCH_BYTES)
 // on `device`, which must be current; looked up on the first call per device.
 cudaError_t static_scratch(int device, void **ptr);
+
+// Graph view of an instance for the learned restart proposal (device arrays).
+struct GraphView {
+    int device;
+    int n, m;
+    const int32_t *row_ptr;   // constraint -> literals (CSR)
+    const uint32_t *lits;     // variable | negated << 31
+    const int32_t *var_ptr;   // variable -> occurrences (transposed CSR)
+    const uint32_t *var_occ;  // constraint | negated << 31
+    const float *fv;          // [n, 8] variable features
+    const float *fc;          // [m, 8] constraint features
+    const float *inv_deg;     // [n] 1 / occurrences (0 if none)
+    const float *inv_len;     // [m] 1 / length
+};
+
+// Build the graph view on first use (host preprocessing + one upload), then
+// return it.  Returns an ffsat status code.
+int instance_graph(::ffsat_instance *inst, GraphView *out);
+// Record an error message for ffsat_last_error(); returns code.
+int set_error(int code, const char *msg);
 
 // Exact checker: one CTA per point.
 cudaError_t launch_check(const DevView &V, bool f64, int B, const void *x, uint8_t *sat, int32_t *n_unsat,

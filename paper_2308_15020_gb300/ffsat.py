@@ -51,6 +51,15 @@ SYMBOLS = (
     "ffsat_batch_eval_grad",
     "ffsat_batch_step",
     "ffsat_batch_free",
+    "ffsat_mpnn_create",
+    "ffsat_mpnn_num_params",
+    "ffsat_mpnn_get_params",
+    "ffsat_mpnn_set_params",
+    "ffsat_mpnn_forward",
+    "ffsat_mpnn_loss_grad",
+    "ffsat_mpnn_adam_step",
+    "ffsat_restart_from_proposal",
+    "ffsat_mpnn_free",
     "ffsat_sync_status",
     "ffsat_instance_info",
     "ffsat_last_launch_count",
@@ -131,6 +140,25 @@ def lib():
         L.ffsat_batch_step.restype = C.c_int
         L.ffsat_batch_free.argtypes = [_vp]
         L.ffsat_batch_free.restype = None
+        L.ffsat_mpnn_create.argtypes = [C.c_int32, C.c_uint64, C.POINTER(_vp)]
+        L.ffsat_mpnn_create.restype = C.c_int
+        L.ffsat_mpnn_num_params.argtypes = [_vp]
+        L.ffsat_mpnn_num_params.restype = C.c_int32
+        L.ffsat_mpnn_get_params.argtypes = [_vp, _vp]
+        L.ffsat_mpnn_get_params.restype = C.c_int
+        L.ffsat_mpnn_set_params.argtypes = [_vp, _vp]
+        L.ffsat_mpnn_set_params.restype = C.c_int
+        L.ffsat_mpnn_forward.argtypes = [_vp, _vp, _vp, _vp]
+        L.ffsat_mpnn_forward.restype = C.c_int
+        L.ffsat_mpnn_loss_grad.argtypes = [_vp, _vp, _vp, _vp, _vp, _vp, _vp]
+        L.ffsat_mpnn_loss_grad.restype = C.c_int
+        L.ffsat_mpnn_adam_step.argtypes = [_vp, C.c_float, _vp]
+        L.ffsat_mpnn_adam_step.restype = C.c_int
+        L.ffsat_restart_from_proposal.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, C.c_float, _vp, C.c_uint64,
+                                                  C.c_uint64, C.c_uint64, _vp]
+        L.ffsat_restart_from_proposal.restype = C.c_int
+        L.ffsat_mpnn_free.argtypes = [_vp]
+        L.ffsat_mpnn_free.restype = None
         L.ffsat_sync_status.argtypes = [_vp, _vp]
         L.ffsat_sync_status.restype = C.c_int
         L.ffsat_instance_info.argtypes = [_vp, C.POINTER(Info)]
@@ -368,6 +396,79 @@ class Batch:
         a = StepArgs(int(T), int(restart), float(lr), int(seed) & (2**64 - 1), int(epoch), 0)
         _check(lib().ffsat_batch_step(self.handle, io, dt, C.byref(a), _stream(stream)))
         return solved, n_unsat
+
+
+class MPNN:
+    """The learned restart proposal network (``ffsat_mpnn_*``)."""
+
+    def __init__(self, layers: int = 3, seed: int = 0):
+        h = _vp()
+        _check(lib().ffsat_mpnn_create(int(layers), int(seed) & (2**64 - 1), C.byref(h)))
+        self.handle = h.value
+        self.layers = layers
+
+    def free(self):
+        if getattr(self, "handle", None):
+            lib().ffsat_mpnn_free(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def num_params(self) -> int:
+        return int(lib().ffsat_mpnn_num_params(self.handle))
+
+    def get_params(self):
+        import numpy as np
+
+        p = np.zeros(self.num_params(), dtype=np.float32)
+        _check(lib().ffsat_mpnn_get_params(self.handle, p.ctypes.data))
+        return p
+
+    def set_params(self, p):
+        import numpy as np
+
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        if p.shape != (self.num_params(),):
+            raise ValueError("wrong parameter count")
+        _check(lib().ffsat_mpnn_set_params(self.handle, p.ctypes.data))
+
+    def forward(self, inst: Instance, x0=None, stream=None):
+        import torch
+
+        if x0 is None:
+            x0 = torch.empty(inst.n, dtype=torch.float32, device="cuda")
+        _check(lib().ffsat_mpnn_forward(self.handle, inst.handle, x0.data_ptr(), _stream(stream)))
+        return x0
+
+    def loss_grad(self, inst: Instance, target, loss=None, x0=None, want_host_grad: bool = False, stream=None):
+        """(loss tensor, proposal tensor, host gradient or None)."""
+        import numpy as np
+        import torch
+
+        _need_cuda_contig(target, "target")
+        if loss is None:
+            loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        if x0 is None:
+            x0 = torch.empty(inst.n, dtype=torch.float32, device="cuda")
+        gh = np.zeros(self.num_params(), dtype=np.float32) if want_host_grad else None
+        _check(lib().ffsat_mpnn_loss_grad(self.handle, inst.handle, target.data_ptr(), loss.data_ptr(), x0.data_ptr(),
+                                          None if gh is None else gh.ctypes.data, _stream(stream)))
+        return loss, x0, gh
+
+    def adam_step(self, lr: float, stream=None):
+        _check(lib().ffsat_mpnn_adam_step(self.handle, float(lr), _stream(stream)))
+
+
+def restart_from_proposal(inst: Instance, x, proposal, noise: float, solved=None, seed: int = 0, epoch: int = 0,
+                          b_offset: int = 0, stream=None):
+    _need_cuda_contig(x, "x")
+    _check(lib().ffsat_restart_from_proposal(inst.handle, x.shape[0], x.data_ptr(), _dtype_code(x), proposal.data_ptr(),
+                                             float(noise), _ptr(solved), int(seed) & (2**64 - 1), int(epoch),
+                                             int(b_offset), _stream(stream)))
 
 
 def load_instance(inst, **kw) -> Instance:

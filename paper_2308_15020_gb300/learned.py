@@ -1,0 +1,184 @@
+"""Learned restart proposal: data from our own CLS runs, training with the
+library's network kernels, and the A/B time-to-SAT protocol.
+
+Every device computation runs in the CUDA library (ffsat_step, ffsat_check,
+the ffsat_mpnn_* kernels and ffsat_restart_from_proposal); this module only
+orchestrates them.  PyTorch supplies device buffers.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from . import ffsat, gen
+
+
+@dataclass
+class CLSConfig:
+    B: int = 64          # restart points per round
+    T: int = 100         # projected-GD iterations per round
+    lr: float = 0.1
+    max_rounds: int = 30
+    noise: float = 0.7   # proposal restarts: x = clip(p + noise * u)
+    seed: int = 1
+
+
+def best_point(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optional[ffsat.MPNN] = None):
+    """Run CLS rounds (uniform restarts, or restarts around the network's proposal);
+    return (signs of the best point found, its #unsat, rounds)."""
+    import torch
+
+    x = torch.zeros(cfg.B, n, dtype=torch.float32, device="cuda")
+    prop = None
+    if net is None:
+        h.step(x, T=0, lr=cfg.lr, seed=seed, epoch=0, restart=True)  # uniform initial points
+    else:
+        prop = net.forward(h)
+        ffsat.restart_from_proposal(h, x, prop, cfg.noise, seed=seed, epoch=0)
+    best, best_u, rounds = None, math.inf, 0
+    for r in range(cfg.max_rounds):
+        rounds = r + 1
+        solved, nun = h.step(x, T=cfg.T, lr=cfg.lr, seed=seed, epoch=r + 1, restart=False)
+        u = nun.cpu().numpy()
+        b = int(np.argmin(u))
+        if u[b] < best_u:
+            best_u = int(u[b])
+            best = torch.where(x[b] < 0, -1.0, 1.0)
+        if best_u == 0:
+            break
+        if net is None:
+            h.step(x, T=0, lr=cfg.lr, seed=seed, epoch=r + 1, restart=True)  # check and uniform restart
+        else:
+            ffsat.restart_from_proposal(h, x, prop, cfg.noise, solved=solved, seed=seed, epoch=r + 1)
+    return best, best_u, rounds
+
+
+def collect(instances, cfg: CLSConfig, net: Optional[ffsat.MPNN] = None, handles=None):
+    """Targets for training: for each instance, the signs of the best point the
+    CLS finds (with uniform restarts, or with the network's proposals)."""
+    data = []
+    for k, inst in enumerate(instances):
+        h = handles[k] if handles is not None else ffsat.Instance(inst)
+        t, u, _ = best_point(h, inst.n, cfg, cfg.seed + 1000 * k, net)
+        data.append((h, t, u))
+    return data
+
+
+def self_train(net: ffsat.MPNN, instances, cfg: CLSConfig, rounds: int = 2, epochs: int = 6, lr: float = 2e-3):
+    """Train on CLS near-solutions; then regenerate the targets with CLS runs that
+    restart around the current proposal and continue training (rounds times).
+    Returns the per-round mean #unsat of the targets and the losses."""
+    data = collect(instances, cfg)
+    handles = [d[0] for d in data]
+    hist = [float(np.mean([d[2] for d in data]))]
+    losses = train(net, data, epochs, lr)
+    for _ in range(rounds - 1):
+        data = collect(instances, cfg, net, handles)
+        hist.append(float(np.mean([d[2] for d in data])))
+        losses += train(net, data, epochs, lr)
+    return hist, losses
+
+
+def train(net: ffsat.MPNN, data, epochs: int = 5, lr: float = 2e-3, seed: int = 0) -> List[float]:
+    """Adam on the logistic loss of the proposal against the collected signs."""
+    rng = np.random.default_rng(seed)
+    losses = []
+    for _ in range(epochs):
+        tot = 0.0
+        for i in rng.permutation(len(data)):
+            h, t, _ = data[i]
+            loss, _, _ = net.loss_grad(h, t)
+            net.adam_step(lr)
+            tot += float(loss.item())
+        losses.append(tot / max(1, len(data)))
+    return losses
+
+
+@dataclass
+class SatRun:
+    solved: bool
+    seconds: float
+    rounds: int
+
+
+def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optional[ffsat.MPNN] = None) -> SatRun:
+    """Wall time until some point's sign vector is a model (Alg. 1), with uniform
+    restarts (net None) or restarts drawn around the network's proposal."""
+    import torch
+
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x = torch.zeros(cfg.B, n, dtype=torch.float32, device="cuda")
+    prop = None
+    if net is None:
+        h.step(x, T=0, lr=cfg.lr, seed=seed, epoch=0, restart=True)
+    else:
+        prop = net.forward(h)
+        ffsat.restart_from_proposal(h, x, prop, cfg.noise, seed=seed, epoch=0)
+    for r in range(cfg.max_rounds):
+        solved, _ = h.step(x, T=cfg.T, lr=cfg.lr, seed=seed, epoch=r + 1, restart=net is None)
+        if bool(solved.any().item()):
+            torch.cuda.synchronize()
+            return SatRun(True, time.perf_counter() - t0, r + 1)
+        if net is not None:
+            ffsat.restart_from_proposal(h, x, prop, cfg.noise, solved=solved, seed=seed, epoch=r + 1)
+    torch.cuda.synchronize()
+    return SatRun(False, time.perf_counter() - t0, cfg.max_rounds)
+
+
+@dataclass
+class ABResult:
+    uniform: List[SatRun] = field(default_factory=list)
+    learned: List[SatRun] = field(default_factory=list)
+
+    @staticmethod
+    def _median(runs):
+        v = [r.seconds if r.solved else math.inf for r in runs]
+        return float(np.median(v)) if v else math.nan
+
+    def summary(self):
+        return {
+            "instances": len(self.uniform),
+            "median_time_to_sat_s": {"uniform": self._median(self.uniform), "learned": self._median(self.learned)},
+            "median_rounds": {"uniform": float(np.median([r.rounds for r in self.uniform])),
+                              "learned": float(np.median([r.rounds for r in self.learned]))},
+            "solved": {"uniform": sum(r.solved for r in self.uniform),
+                       "learned": sum(r.solved for r in self.learned)},
+        }
+
+
+def ab_test(net: ffsat.MPNN, instances, cfg: CLSConfig) -> ABResult:
+    """Held-out A/B: the same instances and seeds with uniform and learned restarts."""
+    res = ABResult()
+    for k, inst in enumerate(instances):
+        h = ffsat.Instance(inst)
+        seed = cfg.seed + 7919 * k
+        time_to_sat(h, inst.n, cfg, seed, None)  # warm the instance's kernels and graph data
+        res.uniform.append(time_to_sat(h, inst.n, cfg, seed, None))
+        res.learned.append(time_to_sat(h, inst.n, cfg, seed, net))
+    return res
+
+
+def sign_agreement(net: ffsat.MPNN, instances) -> float:
+    """Mean fraction of variables whose proposal sign matches the planted assignment."""
+    vals = []
+    for inst in instances:
+        h = ffsat.Instance(inst)
+        p = net.forward(h).cpu().numpy()
+        vals.append(float(np.mean(np.where(p < 0, -1, 1) == inst.planted)))
+    return float(np.mean(vals))
+
+
+def planted_family(count: int, n: int, seed0: int):
+    """CNF-XOR instances of the n=2000 shape (m = 4.2 n clauses, n/10 XORs), planted."""
+    return [gen.cnf_xor_2000(seed0 + i, planted=True, n=n) for i in range(count)]
+
+
+def planted_3sat_family(count: int, n: int, seed0: int, ratio: float = 4.2):
+    """Planted random 3-SAT at the given clause ratio."""
+    return [gen.random_ksat(n, int(round(ratio * n)), 3, seed0 + i, planted=gen.planted_assignment(n, seed0 + i))
+            for i in range(count)]

@@ -1,0 +1,91 @@
+"""The learned restart proposal's CUDA forward/backward against the FP64 oracle,
+its training, and the proposal restart."""
+import numpy as np
+import pytest
+
+import mpnn_oracle as MO
+import oracle as O
+from paper_2308_15020_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _small():
+    return gen.concat([gen.random_ksat(80, 300, 3, 4), gen.random_xor(80, 10, 3, 12, 4, signs=True),
+                       gen.random_atleast(80, 6, 5, 30, 4)])
+
+
+def test_loss_and_gradient_match_oracle():
+    from paper_2308_15020_gb300 import ffsat
+
+    inst = _small()
+    h = ffsat.Instance(inst)
+    net = ffsat.MPNN(layers=3, seed=1)
+    rng = np.random.default_rng(2)
+    p = (rng.normal(0, 0.2, net.num_params())).astype(np.float32)
+    net.set_params(p)
+    t = np.where(rng.random(inst.n) < 0.5, -1.0, 1.0)
+    loss, x0, g = net.loss_grad(h, torch.from_numpy(t.astype(np.float32)).cuda(), want_host_grad=True)
+    lo, go, xo = MO.loss_and_grad(p.astype(np.float64), inst, t, 3, bf16_weights=True)
+    assert abs(float(loss.item()) - lo) <= 1e-5 * max(1.0, abs(lo))
+    assert np.max(np.abs(x0.cpu().numpy() - xo)) < 1e-4
+    scale = np.max(np.abs(go))
+    assert np.all(np.abs(g - go) <= 1e-4 * scale + 1e-3 * np.abs(go)), float(np.max(np.abs(g - go)) / scale)
+    x1 = net.forward(h)
+    assert torch.equal(x1, x0)
+
+
+def test_training_reduces_loss():
+    from paper_2308_15020_gb300 import ffsat
+
+    inst = gen.cnf_xor_2000(5, planted=True, n=400)
+    h = ffsat.Instance(inst)
+    net = ffsat.MPNN(layers=3, seed=3)
+    t = torch.from_numpy(inst.planted.astype(np.float32)).cuda()
+    first = None
+    for it in range(60):
+        loss, _, _ = net.loss_grad(h, t)
+        net.adam_step(3e-3)
+        if first is None:
+            first = float(loss.item())
+    last = float(net.loss_grad(h, t)[0].item())
+    assert last < 0.8 * first, (first, last)
+
+
+def test_proposal_restart_is_exact():
+    from paper_2308_15020_gb300 import ffsat
+
+    inst = gen.uniform_3sat_100(1)
+    h = ffsat.Instance(inst)
+    prop = np.random.default_rng(0).uniform(-1, 1, inst.n).astype(np.float32)
+    x = torch.zeros(5, inst.n, device="cuda")
+    solved = torch.tensor([0, 1, 0, 0, 1], dtype=torch.uint8, device="cuda")
+    ffsat.restart_from_proposal(h, x, torch.from_numpy(prop).cuda(), 0.5, solved=solved, seed=9, epoch=4, b_offset=20)
+    got = x.cpu().numpy()
+    for b in range(5):
+        if b in (1, 4):
+            assert np.all(got[b] == 0)
+        else:
+            u = np.array([O.uniform(9, 4, 20 + b, v) for v in range(inst.n)], dtype=np.float32)
+            want = np.clip(prop + np.float32(0.5) * u, -1, 1)
+            assert np.array_equal(got[b], want)
+
+
+def test_learned_proposal_ab_small():
+    """Train on near-solutions the CLS finds on small planted 3-SAT instances, then
+    compare uniform and learned restarts on held-out instances (same seeds)."""
+    from paper_2308_15020_gb300 import ffsat, learned
+
+    cfg = learned.CLSConfig(B=64, T=200, lr=0.01, max_rounds=8, seed=5, noise=0.7)
+    train_set = learned.planted_3sat_family(32, 250, 100)
+    net = ffsat.MPNN(layers=3, seed=11)
+    hist, losses = learned.self_train(net, train_set, cfg, rounds=2, epochs=6, lr=3e-3)
+    assert losses[-1] < losses[0]
+    held = learned.planted_3sat_family(8, 300, 900)
+    agree = learned.sign_agreement(net, held)
+    res = learned.ab_test(net, held, cfg)
+    summ = res.summary()
+    print("targets mean #unsat per round", hist, "held-out sign agreement", agree, "A/B", summ)
+    assert agree > 0.6, agree
+    assert summ["solved"]["learned"] >= summ["solved"]["uniform"]

@@ -100,6 +100,23 @@ def test_saddle_example_objective():
     assert np.allclose(f1, [_poly2(g["F_after"], *p) for p in pts], atol=1e-15)
 
 
+def test_erwa_saddle_and_local_examples():
+    """Prop. "Adaptive weight" with alpha = 0.4 reproduces the weights printed in
+    the saddle and local-optimum examples from their unsatisfaction scores."""
+    sad = golden("saddle_example.txt")
+    inst = gen.from_lists(2, [(gen.OR, 0, [1, -2]), (gen.XOR, 1, [-1, 2])])
+    # at the saddle's sign vector c1 is satisfied and c2 violated (r = (0, 1))
+    x = fl(sad["stationary"])[None]
+    U = O.unsat_counts(inst, x)
+    assert list(U) == [0, 1]
+    assert np.allclose(O.erwa(U, [1.0, 1.0], 0.4), fl(sad["weights_after"]), atol=1e-15)
+    loc = golden("local_example.txt")
+    inst = gen.from_lists(4, [(gen.XOR, 1, [1, 2]), (gen.XOR, 1, [2, 3]), (gen.XOR, 1, [3, 4])])
+    U = O.unsat_counts(inst, fl(loc["point"])[None])
+    assert list(U) == [0, 1, 0]
+    assert np.allclose(O.erwa(U, [1.0, 1.0, 1.0], 0.4), fl(loc["weights_after"]), atol=1e-15)
+
+
 def test_local_optimum_example_gradient():
     g = golden("local_example.txt")
     inst = gen.from_lists(4, [(gen.XOR, 1, [1, 2]), (gen.XOR, 1, [2, 3]), (gen.XOR, 1, [3, 4])])
