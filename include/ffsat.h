@@ -89,6 +89,12 @@ typedef struct ffsat_step_args {
     uint64_t seed;     /* restart seed */
     uint64_t epoch;    /* outer-round counter (part of the restart draw's key) */
     uint64_t b_offset; /* global index of point 0, so that sharded runs draw alike */
+    /* Device int32 [n_cons] or NULL.  When set, the exact check that ends the
+     * call adds to unsat_counts[c] the number of the B points (after their T
+     * iterations, before any restart) whose sign vector violates c: the
+     * unsatisfaction counts U_c of the ERWA weighting (Sec. 5).  The caller
+     * zeroes the array; ffsat_batch_step ignores the field. */
+    int32_t *unsat_counts;
 } ffsat_step_args;
 
 typedef struct ffsat_info {
@@ -193,6 +199,45 @@ int ffsat_step_noalloc(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, 
  * n_unsat[b] = number of violated constraints.  Either output may be NULL. */
 int ffsat_check(ffsat_instance *inst, int32_t B, const void *x, int32_t dtype, uint8_t *sat, int32_t *n_unsat,
                 void *stream);
+
+/* ---- restart heuristics (Sec. 5: weighting and rephasing) ---------------------------- */
+
+/* Rephasing phases (Sec. 5, "Rephasing Heuristics"). */
+#define FFSAT_PHASE_ORIGINAL 0 /* keep the point the previous round ended at */
+#define FFSAT_PHASE_FLIPPED 1  /* negate every coordinate */
+#define FFSAT_PHASE_RANDOM 2   /* a fresh uniform draw from [-1, 1)^n */
+
+/* U[c] = number of the B points whose sign vector violates constraint c: the
+ * unsatisfaction counts of the ERWA weighting (Sec. 5, "Weighting Heuristics").
+ *   x: device [B, n] of dtype, read only;  U: device int32 [n_cons], overwritten.
+ * ffsat_step produces the same counts inside its final check when
+ * ffsat_step_args.unsat_counts is set. */
+int ffsat_unsat_counts(ffsat_instance *inst, int32_t B, const void *x, int32_t dtype, int32_t *U, void *stream);
+
+/* ERWA update of every constraint weight (Prop. "Adaptive weight"):
+ *   w_c <- (1 - alpha) w_c + alpha r_c,  r_c = U_c / max_c' U_c'  (r = 0 when max U = 0),
+ * computed in FP64 on the device (each operation rounded, no contraction) and
+ * written to every device copy of the weights; F, its gradient and ffsat_step
+ * use the new weights from the next call on the stream.  Negative U_c count as 0.
+ *   U: device int32 [n_cons];  alpha in [0, 1] (the paper uses 0.4).
+ * No host synchronisation and no allocation.  The host-side weights given at
+ * load or by ffsat_set_weights are not updated (read them with
+ * ffsat_get_weights); ffsat_set_weights overwrites the device weights again. */
+int ffsat_erwa_update(ffsat_instance *inst, const int32_t *U, double alpha, void *stream);
+
+/* Rephase the restart points (Sec. 5, "Rephasing Heuristics"): every point b
+ * with solved == NULL or solved[b] == 0 gets phase
+ *   FFSAT_PHASE_ORIGINAL: x_b unchanged;  FFSAT_PHASE_FLIPPED: x_b <- -x_b;
+ *   FFSAT_PHASE_RANDOM: x_b <- uniform draw on the 2^-23 grid of [-1, 1), the
+ *   generator and key (seed, epoch, b_offset + b) of ffsat_step's restarts.
+ *   x: device [B, n] of dtype, updated in place;  solved: device uint8 [B] or NULL.
+ * Errors: FFSAT_ERR_ARG for a bad phase, dtype or NULL x with B > 0. */
+int ffsat_rephase(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, int32_t phase, const uint8_t *solved,
+                  uint64_t seed, uint64_t epoch, uint64_t b_offset, void *stream);
+
+/* Copy the current device weights (after ERWA updates) into a HOST array of
+ * n_cons doubles.  Synchronises the device. */
+int ffsat_get_weights(ffsat_instance *inst, double *weights);
 
 /* ---- several instances of uneven size in one launch ---------------------------------- */
 

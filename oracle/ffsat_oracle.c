@@ -589,6 +589,22 @@ double orc_uniform(uint64_t seed, uint64_t epoch, uint64_t b, uint64_t v) {
     return ldexp((double)u, -23);
 }
 
+int orc_rephase(int32_t n, int32_t B, double *x, int phase, const uint8_t *solved,
+                uint64_t seed, uint64_t epoch, uint64_t b_offset) {
+    if (phase < 0 || phase > 2) return -1;
+    for (int32_t b = 0; b < B; ++b) {
+        if (solved && solved[b]) continue;
+        double *xb = x + (size_t)b * (size_t)n;
+        for (int32_t v = 0; v < n; ++v) {
+            if (phase == 1)
+                xb[v] = -xb[v];
+            else if (phase == 2)
+                xb[v] = orc_uniform(seed, epoch, b_offset + (uint64_t)b, (uint64_t)v);
+        }
+    }
+    return 0;
+}
+
 int orc_step(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *lits,
              const uint8_t *type, const int32_t *param, const double *w,
              int32_t B, double *x, int32_t T, double lr,

@@ -124,6 +124,13 @@ uint64_t orc_splitmix64(uint64_t state);
  * in both float and double. */
 double orc_uniform(uint64_t seed, uint64_t epoch, uint64_t b, uint64_t v);
 
+/* Rephasing (Sec. "Rephasing Heuristics"): every point b with solved == NULL or
+ * solved[b] == 0 takes phase 0 = original (x_b kept), 1 = flipped (x_b = -x_b)
+ * or 2 = random (x_b[v] = orc_uniform(seed, epoch, b_offset + b, v)).
+ * Returns 0, or -1 for an unknown phase. */
+int orc_rephase(int32_t n, int32_t B, double *x, int phase, const uint8_t *solved,
+                uint64_t seed, uint64_t epoch, uint64_t b_offset);
+
 /* One outer round of Alg. 1 with fixed-step projected gradient descent
  * (App. A.3, Alg. "PGFP" without the line search): T times
  * x <- clip(x - lr * grad F(x), -1, 1); then the exact check; solved points keep

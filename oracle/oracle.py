@@ -57,6 +57,8 @@ def lib():
         L.orc_unsat_counts.restype = C.c_int
         L.orc_erwa.argtypes = [C.c_int32, _i32, C.c_double, _dp]
         L.orc_erwa.restype = None
+        L.orc_rephase.argtypes = [C.c_int32, C.c_int32, _dp, C.c_int, _u8, C.c_uint64, C.c_uint64, C.c_uint64]
+        L.orc_rephase.restype = C.c_int
         L.orc_splitmix64.argtypes = [C.c_uint64]
         L.orc_splitmix64.restype = C.c_uint64
         L.orc_uniform.argtypes = [C.c_uint64] * 4
@@ -231,6 +233,18 @@ def erwa(U, w, alpha: float = 0.4):
     w = _f64(w).copy()
     lib().orc_erwa(len(w), _p(U, _i32), alpha, _p(w, _dp))
     return w
+
+
+def rephase(x, phase: int, solved=None, seed: int = 0, epoch: int = 0, b_offset: int = 0):
+    """Sec. "Rephasing Heuristics": original (0), flipped (1) or random (2) phase
+    for the unsolved points; returns the new points (float64)."""
+    x = _f64(np.atleast_2d(x)).copy()
+    s = None if solved is None else np.ascontiguousarray(solved, dtype=np.uint8)
+    rc = lib().orc_rephase(x.shape[1], x.shape[0], _p(x, _dp), int(phase), None if s is None else _p(s, _u8),
+                           seed & 0xFFFFFFFFFFFFFFFF, epoch, b_offset)
+    if rc != 0:
+        raise ValueError("oracle: unknown phase")
+    return x
 
 
 def splitmix64(state: int) -> int:

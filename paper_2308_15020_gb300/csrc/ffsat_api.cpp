@@ -15,6 +15,7 @@
 
 #include "ffsat.h"
 #include "ffsat_internal.h"
+#include "heuristics.h"
 
 using namespace ffsat;
 
@@ -158,6 +159,7 @@ struct ffsat_instance {
     unsigned char *d_arena = nullptr;
     size_t arena_bytes = 0;
     size_t off_clause_wd = 0, off_seg_wd = 0, off_cons_wd = 0;
+    size_t off_f_const = 0, off_cls = 0, off_slot = 0, off_umax = 0;
     int32_t *d_status = nullptr;
     int32_t *d_node_ids = nullptr, *d_closed_ids = nullptr;
     int32_t n_node_ids = 0, n_closed_ids = 0;
@@ -384,7 +386,9 @@ FusedFn launcher_for(bool f64, int nr) {
 }
 
 // Scales of the two-word fixed-point accumulator: a contribution is bounded by
-// its weight (|dFE/dy| <= 1, with a margin for rounding), so with S1 =
+// its weight (|dFE/dy| <= 1, with a margin for rounding).  Each weight is
+// bounded by b_c = max(w_c, 1), which also bounds every later ERWA weight
+// ((1 - a) w + a r <= b_c for r in [0, 1]); with wmax and Dmax taken over b_c, S1 =
 // min(21 - ceil(log2 wmax), 30 - ceil(log2 Dmax)) the hi word is rounded
 // exactly (|c 2^S1| < 2^22) and never exceeds 2^30 in sum (Dmax = largest
 // weighted variable degree); the residual lies in [-1/2, 1/2], so with
@@ -395,11 +399,12 @@ void fixed_point_scales(ffsat_instance *I) {
     double wmax = 0.0;
     for (int32_t c = 0; c < I->m; ++c) {
         if (I->cls[c] == CLS_CONST) continue;
-        wmax = std::max(wmax, I->w[c]);
+        const double bc = std::max(I->w[c], 1.0);
+        wmax = std::max(wmax, bc);
         for (int64_t i = I->row_ptr[c]; i < I->row_ptr[c + 1]; ++i) {
             const int32_t l = I->lits_in[i];
             const int32_t v = (l > 0 ? l : -l) - 1;
-            D[v] += I->w[c];
+            D[v] += bc;
             deg[v] += 1;
         }
     }
@@ -893,6 +898,10 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     const size_t o_rp = A.put(rp32), o_lits = A.put(lp32), o_type = A.put(P->type), o_par = A.put(par32);
     const size_t o_ctab = A.put(cons_tab);
     P->off_cons_wd = A.put(P->cons_wd);
+    P->off_f_const = A.put(std::vector<double>{P->f_const, P->f_const_plain});
+    P->off_cls = A.put(P->cls);
+    P->off_slot = A.put(P->slot);
+    P->off_umax = A.put(std::vector<int32_t>{0});
     const size_t o_nid = A.put(node_c), o_cid = A.put(closed_ids);
     P->arena_bytes = A.host.size();
     CUDA_TRY(cudaMalloc(&P->d_arena, P->arena_bytes));
@@ -912,13 +921,11 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     V.tab_d = reinterpret_cast<const double *>(base + o_td);
     V.pad_y_f = opt.form == FFSAT_FORM_PAPER ? 0.0f : 1.0f;
     V.pad_y_d = opt.form == FFSAT_FORM_PAPER ? 0.0 : 1.0;
-    V.f_const_d = P->f_const;
-    V.f_const_plain = P->f_const_plain;
+    V.f_const = reinterpret_cast<const double *>(base + P->off_f_const);
     V.fix_s1 = P->fix_s1;
     V.fix_s2 = P->fix_s2;
     V.fix_i1 = P->fix_i1;
     V.fix_i12 = P->fix_i12;
-    V.f_const_f = (float)P->f_const;
     V.row_ptr = reinterpret_cast<const int32_t *>(base + o_rp);
     V.lits = reinterpret_cast<const int32_t *>(base + o_lits);
     V.type = reinterpret_cast<const uint8_t *>(base + o_type);
@@ -986,15 +993,14 @@ int ffsat_set_weights(ffsat_instance *I, const double *weights) {
     CUDA_TRY(cudaMemcpy(base + I->off_clause_wd, I->clause_wd.data(), I->clause_wd.size() * sizeof(double), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(base + I->off_seg_wd, I->seg_wd.data(), I->seg_wd.size() * sizeof(double), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(base + I->off_cons_wd, I->cons_wd.data(), I->cons_wd.size() * sizeof(double), cudaMemcpyHostToDevice));
-    I->V32.f_const_d = I->V64.f_const_d = I->f_const;
-    I->V32.f_const_plain = I->V64.f_const_plain = I->f_const_plain;
+    const double fc[2] = {I->f_const, I->f_const_plain};
+    CUDA_TRY(cudaMemcpy(base + I->off_f_const, fc, sizeof(fc), cudaMemcpyHostToDevice));
     for (DevView *W : {&I->V32, &I->V64}) {
         W->fix_s1 = I->fix_s1;
         W->fix_s2 = I->fix_s2;
         W->fix_i1 = I->fix_i1;
         W->fix_i12 = I->fix_i12;
     }
-    I->V32.f_const_f = I->V64.f_const_f = (float)I->f_const;
     return FFSAT_OK;
 }
 
@@ -1074,6 +1080,7 @@ int ffsat_step(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat
     a.sp.seed = args->seed;
     a.sp.epoch = args->epoch;
     a.sp.b_offset = args->b_offset;
+    a.unsat_counts = args->unsat_counts;
     if (mode != SMEM_FULL) {
         const size_t need = (size_t)B * (size_t)I->n * elem;
         if (need > I->scratch_bytes) {
@@ -1120,6 +1127,7 @@ int ffsat_step_noalloc(ffsat_instance *I, int32_t B, void *x, int32_t dtype, con
     a.sp.seed = args->seed;
     a.sp.epoch = args->epoch;
     a.sp.b_offset = args->b_offset;
+    a.unsat_counts = args->unsat_counts;
     if (mode != SMEM_FULL && mode != SMEM_RES) {
         const size_t need = (size_t)B * (size_t)I->n * elem;
         if (need > (size_t)FFSAT_STATIC_SCRATCH_BYTES)
@@ -1147,8 +1155,87 @@ int ffsat_check(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, uint
     if (B == 0) return FFSAT_OK;
     if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
     CUDA_TRY(cudaSetDevice(I->device));
-    CUDA_TRY(launch_check(I->V32, dtype == FFSAT_F64, B, x, sat, n_unsat, static_cast<cudaStream_t>(stream)));
+    CUDA_TRY(launch_check(I->V32, dtype == FFSAT_F64, B, x, sat, n_unsat, nullptr, static_cast<cudaStream_t>(stream)));
     t_launches = 1;
+    return FFSAT_OK;
+}
+
+int ffsat_unsat_counts(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, int32_t *U, void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!I) return fail(FFSAT_ERR_ARG, "instance is NULL");
+    if (B < 0) return fail(FFSAT_ERR_ARG, "B must be >= 0");
+    int rc = check_dtype(dtype);
+    if (rc) return rc;
+    if (I->m == 0) return FFSAT_OK;
+    if (!U) return fail(FFSAT_ERR_ARG, "U is NULL");
+    if (B > 0 && !x) return fail(FFSAT_ERR_ARG, "x is NULL");
+    CUDA_TRY(cudaSetDevice(I->device));
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    CUDA_TRY(cudaMemsetAsync(U, 0, (size_t)I->m * sizeof(int32_t), s));
+    CUDA_TRY(launch_check(I->V32, dtype == FFSAT_F64, B, x, nullptr, nullptr, U, s));
+    t_launches = B > 0 ? 1 : 0;
+    return FFSAT_OK;
+}
+
+int ffsat_erwa_update(ffsat_instance *I, const int32_t *U, double alpha, void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!I) return fail(FFSAT_ERR_ARG, "instance is NULL");
+    if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(FFSAT_ERR_ARG, "alpha must lie in [0, 1]");
+    if (I->m == 0) return FFSAT_OK;
+    if (!U) return fail(FFSAT_ERR_ARG, "U is NULL");
+    CUDA_TRY(cudaSetDevice(I->device));
+    unsigned char *base = I->d_arena;
+    WeightSites W{};
+    W.m = I->m;
+    W.n_images = I->n_images;
+    for (int k = 0; k < I->n_images; ++k) {
+        int4 *img = reinterpret_cast<int4 *>(base + I->off_image[k]);
+        W.clauses[k] = img + I->img_off[k][1];
+        W.segmeta[k] = img + I->img_off[k][2];
+    }
+    W.clause_wd = reinterpret_cast<double *>(base + I->off_clause_wd);
+    W.seg_wd = reinterpret_cast<double *>(base + I->off_seg_wd);
+    W.cons_wd = reinterpret_cast<double *>(base + I->off_cons_wd);
+    W.cls = reinterpret_cast<const int8_t *>(base + I->off_cls);
+    W.slot = reinterpret_cast<const int32_t *>(base + I->off_slot);
+    W.row_ptr = I->V64.row_ptr;
+    W.param = I->V64.param;
+    int nl = 0;
+    CUDA_TRY(launch_erwa(W, U, reinterpret_cast<int32_t *>(base + I->off_umax), alpha,
+                         reinterpret_cast<double *>(base + I->off_f_const), static_cast<cudaStream_t>(stream), &nl));
+    t_launches = nl;
+    return FFSAT_OK;
+}
+
+int ffsat_rephase(ffsat_instance *I, int32_t B, void *x, int32_t dtype, int32_t phase, const uint8_t *solved,
+                  uint64_t seed, uint64_t epoch, uint64_t b_offset, void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!I) return fail(FFSAT_ERR_ARG, "instance is NULL");
+    if (B < 0) return fail(FFSAT_ERR_ARG, "B must be >= 0");
+    int rc = check_dtype(dtype);
+    if (rc) return rc;
+    if (phase != FFSAT_PHASE_ORIGINAL && phase != FFSAT_PHASE_FLIPPED && phase != FFSAT_PHASE_RANDOM)
+        return fail(FFSAT_ERR_ARG, "phase must be FFSAT_PHASE_ORIGINAL, _FLIPPED or _RANDOM");
+    if (B == 0) return FFSAT_OK;
+    if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
+    CUDA_TRY(cudaSetDevice(I->device));
+    int nl = 0;
+    CUDA_TRY(launch_rephase(dtype == FFSAT_F64, x, B, I->n, phase, solved, seed, epoch, b_offset,
+                            static_cast<cudaStream_t>(stream), &nl));
+    t_launches = nl;
+    return FFSAT_OK;
+}
+
+int ffsat_get_weights(ffsat_instance *I, double *weights) {
+    t_err.clear();
+    if (!I || !weights) return fail(FFSAT_ERR_ARG, "NULL argument");
+    if (I->m == 0) return FFSAT_OK;
+    CUDA_TRY(cudaSetDevice(I->device));
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(weights, I->d_arena + I->off_cons_wd, (size_t)I->m * sizeof(double), cudaMemcpyDeviceToHost));
     return FFSAT_OK;
 }
 

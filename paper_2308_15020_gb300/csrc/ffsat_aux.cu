@@ -10,7 +10,7 @@ namespace dev {
 // ---------------------------------------------------------------------------
 template <typename R>
 __global__ void __launch_bounds__(256) check_kernel(const DevView V, int B, const R *__restrict__ x, uint8_t *sat,
-                                                    int32_t *n_unsat) {
+                                                    int32_t *n_unsat, int32_t *U) {
     __shared__ int s_ired[32];
     const int n = V.n;
     for (int b = blockIdx.x; b < B; b += gridDim.x) {
@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(256) check_kernel(const DevView V, int B, cons
         bool bad = false;
         for (int v = threadIdx.x; v < n; v += blockDim.x) bad |= isnan(xrow[v]);
         if (bad) atomicOr(V.status, STATUS_NAN);
-        const int u = block_unsat<R>(V, xrow, s_ired);
+        const int u = block_unsat<R>(V, xrow, s_ired, U);
         if (threadIdx.x == 0) {
             if (sat) sat[b] = (uint8_t)(u == 0);
             if (n_unsat) n_unsat[b] = u;
@@ -30,12 +30,12 @@ __global__ void __launch_bounds__(256) check_kernel(const DevView V, int B, cons
 // ---------------------------------------------------------------------------
 // plain FP64 comparator: naive mapping, one thread per (constraint, point)
 // ---------------------------------------------------------------------------
-__global__ void plain64_init(int B, int n, double *f, double *g, double f_const) {
+__global__ void plain64_init(int B, int n, double *f, double *g, const double *f_const) {
     const size_t tot = (size_t)B * (size_t)n;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x)
         g[i] = 0.0;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < (size_t)B; i += (size_t)gridDim.x * blockDim.x)
-        f[i] = f_const;
+        f[i] = f_const[1];
 }
 
 // Clauses and XOR constraints by their closed forms, all-but-one products by
@@ -125,13 +125,13 @@ __global__ void __launch_bounds__(128) plain64_node(const DevView V, int B, cons
 }  // namespace dev
 
 cudaError_t launch_check(const DevView &V, bool f64, int B, const void *x, uint8_t *sat, int32_t *n_unsat,
-                         cudaStream_t s) {
+                         int32_t *U, cudaStream_t s) {
     if (B <= 0) return cudaSuccess;
     const int grid = B < 65535 * 32 ? B : 65535 * 32;
     if (f64)
-        dev::check_kernel<double><<<grid, 256, 0, s>>>(V, B, static_cast<const double *>(x), sat, n_unsat);
+        dev::check_kernel<double><<<grid, 256, 0, s>>>(V, B, static_cast<const double *>(x), sat, n_unsat, U);
     else
-        dev::check_kernel<float><<<grid, 256, 0, s>>>(V, B, static_cast<const float *>(x), sat, n_unsat);
+        dev::check_kernel<float><<<grid, 256, 0, s>>>(V, B, static_cast<const float *>(x), sat, n_unsat, U);
     return cudaGetLastError();
 }
 
@@ -140,7 +140,7 @@ cudaError_t launch_plain64(const DevView &V, int B, const double *x, double *f, 
                            cudaStream_t s, int *launches) {
     int nl = 0;
     if (B > 0) {
-        dev::plain64_init<<<1024, 256, 0, s>>>(B, V.n, f, g, V.f_const_plain);
+        dev::plain64_init<<<1024, 256, 0, s>>>(B, V.n, f, g, V.f_const);
         ++nl;
         if (n_closed > 0) {
             const size_t tot = (size_t)n_closed * (size_t)B;

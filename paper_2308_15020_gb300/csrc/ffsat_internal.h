@@ -61,10 +61,12 @@ struct DevView {
     const float4 *tab_f;
     const double *tab_d;
     float pad_y_f;   // literal value that makes a node factor exactly 1 (+1 stable form, 0 paper form)
-    float f_const_f; // sum of w FE over constant constraints
+    float pad2;
     double pad_y_d;
-    double f_const_d;
-    double f_const_plain;  // sum of w FE over constant constraints only (plain FP64 path)
+    // device constants of f under the current weights: [0] = sum over clauses of
+    // -w plus sum of w FE over constant constraints (fused kernel), [1] = the
+    // latter alone (plain FP64 path); rewritten on the device by the ERWA update
+    const double *f_const;
     // Two-word fixed-point gradient accumulator of the FP32 shared-resident mode:
     // g = hi / 2^S1 + lo / 2^(S1+S2); fix_s1 = 2^S1, fix_s2 = 2^S2 and the inverses.
     float fix_s1, fix_s2, fix_i1, fix_i12;
@@ -105,6 +107,7 @@ struct FusedArgs {
     StepParams sp;
     uint8_t *solved;
     int32_t *n_unsat;
+    int32_t *unsat_counts;  // step: per-constraint violation counts added by the final check (may be NULL)
 };
 
 // One instance of a batch launch.
@@ -162,7 +165,7 @@ int set_error(int code, const char *msg);
 
 // Exact checker: one CTA per point.
 cudaError_t launch_check(const DevView &V, bool f64, int B, const void *x, uint8_t *sat, int32_t *n_unsat,
-                         cudaStream_t s);
+                         int32_t *U, cudaStream_t s);
 // Plain FP64 comparator; *launches receives the number of kernels enqueued.
 cudaError_t launch_plain64(const DevView &V, int B, const double *x, double *f, double *g, int32_t n_node,
                            const int32_t *node_ids, int32_t n_closed, const int32_t *closed_ids,

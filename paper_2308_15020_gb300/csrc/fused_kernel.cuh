@@ -426,8 +426,9 @@ __device__ __forceinline__ T block_sum(T v, T *red) {
 }
 
 // Exact check of sgn(xrow): number of violated constraints (valid in thread 0).
+// With U set, also adds one to U[c] for every violated constraint c.
 template <typename R>
-__device__ __forceinline__ int block_unsat(const DevView &V, const R *xrow, int *ired) {
+__device__ __forceinline__ int block_unsat(const DevView &V, const R *xrow, int *ired, int32_t *U) {
     int cnt = 0;
     for (int c = threadIdx.x; c < V.m; c += blockDim.x) {
         const int a = __ldg(&V.row_ptr[c]), e = __ldg(&V.row_ptr[c + 1]);
@@ -440,6 +441,7 @@ __device__ __forceinline__ int block_unsat(const DevView &V, const R *xrow, int 
         const int t = __ldg(&V.type[c]), p = __ldg(&V.param[c]);
         const bool ok = t == 0 ? s >= 1 : (t == 1 ? ((s & 1) == (p & 1)) : s >= p);
         cnt += ok ? 0 : 1;
+        if (!ok && U) atomicAdd(&U[c], 1);
     }
     return block_sum(cnt, ired);
 }
@@ -612,7 +614,7 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
         if (!step) {
             if (A.f) {
                 const double tot = block_sum((double)facc, s_red);
-                if (tid == 0) A.f[b] = tot + V.f_const_d;
+                if (tid == 0) A.f[b] = tot + V.f_const[0];
             }
             if constexpr (XG == SMEM_FULL) {
                 if (g_out)
@@ -632,7 +634,7 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
     }
     if (step) {
         const R *xc = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
-        const int unsat = block_unsat<R>(V, xc, s_ired);
+        const int unsat = block_unsat<R>(V, xc, s_ired, A.unsat_counts);
         if (tid == 0) s_ired[0] = unsat;
         __syncthreads();
         const int u = s_ired[0];

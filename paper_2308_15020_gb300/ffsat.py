@@ -22,6 +22,7 @@ FFSAT_F32, FFSAT_F64 = 0, 1
 FFSAT_FORM_STABLE, FFSAT_FORM_PAPER = 0, 1
 FFSAT_MAX_LEN = 512
 FFSAT_STATIC_SCRATCH_BYTES = 32 << 20
+FFSAT_PHASE_ORIGINAL, FFSAT_PHASE_FLIPPED, FFSAT_PHASE_RANDOM = 0, 1, 2
 
 ERRORS = {
     0: "FFSAT_OK",
@@ -47,6 +48,10 @@ SYMBOLS = (
     "ffsat_step",
     "ffsat_step_noalloc",
     "ffsat_check",
+    "ffsat_unsat_counts",
+    "ffsat_erwa_update",
+    "ffsat_rephase",
+    "ffsat_get_weights",
     "ffsat_batch_create",
     "ffsat_batch_eval_grad",
     "ffsat_batch_step",
@@ -81,7 +86,7 @@ class Options(C.Structure):
 
 class StepArgs(C.Structure):
     _fields_ = [("T", C.c_int32), ("restart", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64),
-                ("epoch", C.c_uint64), ("b_offset", C.c_uint64)]
+                ("epoch", C.c_uint64), ("b_offset", C.c_uint64), ("unsat_counts", C.c_void_p)]
 
 
 class BatchIO(C.Structure):
@@ -132,6 +137,15 @@ def lib():
         L.ffsat_step_noalloc.restype = C.c_int
         L.ffsat_check.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
         L.ffsat_check.restype = C.c_int
+        L.ffsat_unsat_counts.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp]
+        L.ffsat_unsat_counts.restype = C.c_int
+        L.ffsat_erwa_update.argtypes = [_vp, _vp, C.c_double, _vp]
+        L.ffsat_erwa_update.restype = C.c_int
+        L.ffsat_rephase.argtypes = [_vp, C.c_int32, _vp, C.c_int32, C.c_int32, _vp, C.c_uint64, C.c_uint64,
+                                    C.c_uint64, _vp]
+        L.ffsat_rephase.restype = C.c_int
+        L.ffsat_get_weights.argtypes = [_vp, _vp]
+        L.ffsat_get_weights.restype = C.c_int
         L.ffsat_batch_create.argtypes = [C.POINTER(_vp), C.c_int32, C.POINTER(_vp)]
         L.ffsat_batch_create.restype = C.c_int
         L.ffsat_batch_eval_grad.argtypes = [_vp, C.POINTER(BatchIO), C.c_int32, _vp]
@@ -257,6 +271,12 @@ class Instance:
         if w.shape != (self.m,):
             raise ValueError("weights must have shape (m,)")
         _check(lib().ffsat_set_weights(self.handle, w.ctypes.data))
+        self._w = w
+
+    @property
+    def host_weights(self):
+        """The weights last given at load or to set_weights (ERWA updates live on the device)."""
+        return self._w
 
     # -- hot path ----------------------------------------------------------------------------
     def eval_grad(self, x, f=None, g=None, want_f: bool = True, want_g: bool = True, stream=None):
@@ -288,8 +308,10 @@ class Instance:
         return f, g
 
     def step(self, x, T: int, lr: float, seed: int = 0, epoch: int = 0, b_offset: int = 0, restart: bool = True,
-             solved=None, n_unsat=None, stream=None):
-        """One round of fixed-step projected GD + exact check + restart, in place on x."""
+             solved=None, n_unsat=None, unsat_counts=None, stream=None):
+        """One round of fixed-step projected GD + exact check + restart, in place on x.
+        With ``unsat_counts`` (int32 [m], zeroed by the caller) the check also adds
+        the per-constraint violation counts of the final points."""
         import torch
 
         _need_cuda_contig(x, "x")
@@ -298,13 +320,14 @@ class Instance:
             solved = torch.empty(B, dtype=torch.uint8, device=x.device)
         if n_unsat is None:
             n_unsat = torch.empty(B, dtype=torch.int32, device=x.device)
-        a = StepArgs(int(T), int(restart), float(lr), int(seed) & (2**64 - 1), int(epoch), int(b_offset))
+        a = StepArgs(int(T), int(restart), float(lr), int(seed) & (2**64 - 1), int(epoch), int(b_offset),
+                     _ptr(self._counts_arg(unsat_counts)))
         _check(lib().ffsat_step(self.handle, B, x.data_ptr(), _dtype_code(x), C.byref(a), solved.data_ptr(),
                                 n_unsat.data_ptr(), _stream(stream)))
         return solved, n_unsat
 
     def step_noalloc(self, x, T: int, lr: float, seed: int = 0, epoch: int = 0, b_offset: int = 0,
-                     restart: bool = True, solved=None, n_unsat=None, stream=None):
+                     restart: bool = True, solved=None, n_unsat=None, unsat_counts=None, stream=None):
         """``step`` through ``ffsat_step_noalloc``: no device allocation, static scratch."""
         import torch
 
@@ -314,7 +337,8 @@ class Instance:
             solved = torch.empty(B, dtype=torch.uint8, device=x.device)
         if n_unsat is None:
             n_unsat = torch.empty(B, dtype=torch.int32, device=x.device)
-        a = StepArgs(int(T), int(restart), float(lr), int(seed) & (2**64 - 1), int(epoch), int(b_offset))
+        a = StepArgs(int(T), int(restart), float(lr), int(seed) & (2**64 - 1), int(epoch), int(b_offset),
+                     _ptr(self._counts_arg(unsat_counts)))
         _check(lib().ffsat_step_noalloc(self.handle, B, x.data_ptr(), _dtype_code(x), C.byref(a), solved.data_ptr(),
                                         n_unsat.data_ptr(), _stream(stream)))
         return solved, n_unsat
@@ -332,6 +356,45 @@ class Instance:
 
     def sync_status(self, stream=None):
         _check(lib().ffsat_sync_status(self.handle, _stream(stream)))
+
+    # -- restart heuristics ------------------------------------------------------------------
+    def _counts_arg(self, U):
+        if U is None:
+            return None
+        import torch
+
+        _need_cuda_contig(U, "unsat_counts")
+        if U.dtype != torch.int32 or U.numel() != self.m:
+            raise ValueError("unsat_counts must be an int32 tensor of m elements")
+        return U
+
+    def unsat_counts(self, x, U=None, stream=None):
+        """U[c] = number of points of x whose sign vector violates constraint c."""
+        import torch
+
+        _need_cuda_contig(x, "x")
+        U = torch.empty(self.m, dtype=torch.int32, device=x.device) if U is None else self._counts_arg(U)
+        _check(lib().ffsat_unsat_counts(self.handle, x.shape[0], x.data_ptr(), _dtype_code(x), _ptr(U),
+                                        _stream(stream)))
+        return U
+
+    def erwa_update(self, U, alpha: float = 0.4, stream=None):
+        """Device ERWA update w <- (1 - alpha) w + alpha U / max U of every weight."""
+        _check(lib().ffsat_erwa_update(self.handle, _ptr(self._counts_arg(U)), float(alpha), _stream(stream)))
+
+    def rephase(self, x, phase: int, solved=None, seed: int = 0, epoch: int = 0, b_offset: int = 0, stream=None):
+        """Original (0) / flipped (1) / random (2) phase for the unsolved points of x, in place."""
+        _need_cuda_contig(x, "x")
+        _check(lib().ffsat_rephase(self.handle, x.shape[0], x.data_ptr(), _dtype_code(x), int(phase), _ptr(solved),
+                                   int(seed) & (2**64 - 1), int(epoch), int(b_offset), _stream(stream)))
+        return x
+
+    def get_weights(self):
+        import numpy as np
+
+        w = np.empty(self.m, dtype=np.float64)
+        _check(lib().ffsat_get_weights(self.handle, w.ctypes.data))
+        return w
 
 
 class Batch:

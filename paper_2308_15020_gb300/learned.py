@@ -25,6 +25,51 @@ class CLSConfig:
     max_rounds: int = 30
     noise: float = 0.7   # proposal restarts: x = clip(p + noise * u)
     seed: int = 1
+    heuristics: bool = True  # ERWA weights + rephasing between rounds (else plain restarts)
+    alpha: float = 0.4       # ERWA decay (Prop. "Adaptive weight")
+    policy: str = "ROF"      # rephasing policy, repeated: R random, O original, F flipped
+
+
+_PHASE = {"O": 0, "F": 1, "R": 2}
+
+
+class _Search:
+    """State of one CLS run on one instance: B points, per-round step, and the
+    restart rule between rounds -- uniform restarts, or (cfg.heuristics) the
+    ERWA update plus the rephasing policy, where the learned arm draws its random
+    phase around the network's proposal instead of uniformly."""
+
+    def __init__(self, h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, prop=None):
+        import torch
+
+        self.h, self.cfg, self.seed, self.prop = h, cfg, seed, prop
+        self.x = torch.zeros(cfg.B, n, dtype=torch.float32, device="cuda")
+        self.U = torch.zeros(h.m, dtype=torch.int32, device="cuda") if cfg.heuristics else None
+        if prop is None:
+            h.rephase(self.x, ffsat.FFSAT_PHASE_RANDOM, seed=seed, epoch=0)
+        else:
+            ffsat.restart_from_proposal(h, self.x, prop, cfg.noise, seed=seed, epoch=0)
+
+    def round(self, r: int, on_checked=None):
+        """One round: T iterations and the exact check (on_checked(x, solved,
+        n_unsat) sees the points here), then the restart rule for the points that
+        are not models.  Returns (solved, n_unsat) of the round."""
+        cfg, h, x = self.cfg, self.h, self.x
+        if self.U is not None:
+            self.U.zero_()
+        solved, nun = h.step(x, T=cfg.T, lr=cfg.lr, seed=self.seed, epoch=r + 1, restart=False,
+                             unsat_counts=self.U)
+        if on_checked is not None:
+            on_checked(x, solved, nun)
+        phase = ffsat.FFSAT_PHASE_RANDOM
+        if cfg.heuristics:
+            h.erwa_update(self.U, cfg.alpha)
+            phase = _PHASE[cfg.policy[r % len(cfg.policy)]]
+        if phase == ffsat.FFSAT_PHASE_RANDOM and self.prop is not None:
+            ffsat.restart_from_proposal(h, x, self.prop, cfg.noise, solved=solved, seed=self.seed, epoch=r + 1)
+        else:
+            h.rephase(x, phase, solved=solved, seed=self.seed, epoch=r + 1)
+        return solved, nun
 
 
 def best_point(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optional[ffsat.MPNN] = None):
@@ -32,28 +77,28 @@ def best_point(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Option
     return (signs of the best point found, its #unsat, rounds)."""
     import torch
 
-    x = torch.zeros(cfg.B, n, dtype=torch.float32, device="cuda")
-    prop = None
-    if net is None:
-        h.step(x, T=0, lr=cfg.lr, seed=seed, epoch=0, restart=True)  # uniform initial points
-    else:
-        prop = net.forward(h)
-        ffsat.restart_from_proposal(h, x, prop, cfg.noise, seed=seed, epoch=0)
-    best, best_u, rounds = None, math.inf, 0
-    for r in range(cfg.max_rounds):
-        rounds = r + 1
-        solved, nun = h.step(x, T=cfg.T, lr=cfg.lr, seed=seed, epoch=r + 1, restart=False)
+    if cfg.heuristics:
+        h.set_weights(h.host_weights)
+    prop = None if net is None else net.forward(h)
+    S = _Search(h, n, cfg, seed, prop)
+    st = {"best": None, "u": math.inf}
+
+    def keep_best(x, solved, nun):
         u = nun.cpu().numpy()
         b = int(np.argmin(u))
-        if u[b] < best_u:
-            best_u = int(u[b])
-            best = torch.where(x[b] < 0, -1.0, 1.0)
-        if best_u == 0:
+        if u[b] < st["u"]:
+            st["u"] = int(u[b])
+            st["best"] = torch.where(x[b] < 0, -1.0, 1.0)
+
+    rounds = 0
+    for r in range(cfg.max_rounds):
+        rounds = r + 1
+        S.round(r, keep_best)
+        if st["u"] == 0:
             break
-        if net is None:
-            h.step(x, T=0, lr=cfg.lr, seed=seed, epoch=r + 1, restart=True)  # check and uniform restart
-        else:
-            ffsat.restart_from_proposal(h, x, prop, cfg.noise, solved=solved, seed=seed, epoch=r + 1)
+    best, best_u = st["best"], st["u"]
+    if cfg.heuristics:
+        h.set_weights(h.host_weights)
     return best, best_u, rounds
 
 
@@ -110,22 +155,17 @@ def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optio
     restarts (net None) or restarts drawn around the network's proposal."""
     import torch
 
+    if cfg.heuristics:
+        h.set_weights(h.host_weights)  # every run starts from the instance's own weights
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    x = torch.zeros(cfg.B, n, dtype=torch.float32, device="cuda")
-    prop = None
-    if net is None:
-        h.step(x, T=0, lr=cfg.lr, seed=seed, epoch=0, restart=True)
-    else:
-        prop = net.forward(h)
-        ffsat.restart_from_proposal(h, x, prop, cfg.noise, seed=seed, epoch=0)
+    prop = None if net is None else net.forward(h)
+    S = _Search(h, n, cfg, seed, prop)
     for r in range(cfg.max_rounds):
-        solved, _ = h.step(x, T=cfg.T, lr=cfg.lr, seed=seed, epoch=r + 1, restart=net is None)
+        solved, _ = S.round(r)
         if bool(solved.any().item()):
             torch.cuda.synchronize()
             return SatRun(True, time.perf_counter() - t0, r + 1)
-        if net is not None:
-            ffsat.restart_from_proposal(h, x, prop, cfg.noise, solved=solved, seed=seed, epoch=r + 1)
     torch.cuda.synchronize()
     return SatRun(False, time.perf_counter() - t0, cfg.max_rounds)
 

@@ -117,6 +117,66 @@ def test_erwa_saddle_and_local_examples():
     assert np.allclose(O.erwa(U, [1.0, 1.0, 1.0], 0.4), fl(loc["weights_after"]), atol=1e-15)
 
 
+def test_erwa_is_the_recency_weighted_average():
+    """Sec. "Weighting Heuristics": from w = 0, t updates give the ERWA sum
+    w^(t) = sum_i alpha (1 - alpha)^(t - i) r^(i) with r^(i) = U^(i) / max U^(i)."""
+    rng = np.random.default_rng(3)
+    m, alpha = 9, 0.4
+    w = np.zeros(m)
+    rs = []
+    for t in range(6):
+        U = rng.integers(0, 20, size=m).astype(np.int32)
+        if t == 2:
+            U[:] = 0  # no violated constraint: r = 0 everywhere
+        rs.append(U / U.max() if U.max() > 0 else np.zeros(m))
+        w = O.erwa(U, w, alpha)
+        ref = sum(alpha * (1 - alpha) ** (t - i) * rs[i] for i in range(t + 1))
+        assert np.allclose(w, ref, rtol=0, atol=1e-14)
+    # decay only when nothing is violated
+    assert np.array_equal(O.erwa(np.zeros(3, np.int32), [1.0, 2.0, 0.5], 0.4), np.array([0.6, 1.2, 0.3]))
+
+
+def test_unsat_counts_brute_force():
+    """U_c counts, over the points, the sign vectors that violate c (checked by
+    direct evaluation of each constraint's Boolean definition)."""
+    inst = gen.concat([gen.random_ksat(12, 30, 3, 5), gen.random_xor(12, 6, 2, 5, 5),
+                       gen.random_atleast(12, 5, 2, 8, 5)])
+    x = gen.uniform_points(11, 12, 4, dtype=np.float64)
+    U = O.unsat_counts(inst, x)
+    rp, lits = inst.row_ptr, inst.lits
+    for c in range(inst.m):
+        cnt = 0
+        for b in range(x.shape[0]):
+            ls = lits[rp[c]:rp[c + 1]]
+            true = [(x[b, abs(l) - 1] < 0) == (l > 0) for l in ls]  # x < 0 encodes True
+            s = sum(true)
+            t, p = inst.ctype[c], inst.param[c]
+            ok = s >= 1 if t == gen.OR else (s % 2 == p % 2 if t == gen.XOR else s >= p)
+            cnt += not ok
+        assert U[c] == cnt, c
+    _, nun = O.check(inst, x)
+    assert U.sum() == nun.sum()
+
+
+def test_rephase_phases():
+    """Sec. "Rephasing Heuristics": original keeps, flipped negates, random draws
+    the same uniform point as the restart of a CLS round; solved points stay."""
+    inst = gen.random_ksat(40, 400, 3, 9)  # unsatisfiable in practice at ratio 10
+    x = gen.uniform_points(6, 40, 2, dtype=np.float64)
+    solved = np.array([0, 1, 0, 0, 1, 0], np.uint8)
+    assert np.array_equal(O.rephase(x, 0, solved), x)
+    xf = O.rephase(x, 1, solved)
+    assert np.array_equal(xf[solved == 1], x[solved == 1]) and np.array_equal(xf[solved == 0], -x[solved == 0])
+    assert np.array_equal(O.rephase(xf, 1, solved), x)
+    xr = O.rephase(x, 2, None, seed=7, epoch=3, b_offset=100)
+    assert np.all((xr >= -1) & (xr < 1)) and np.array_equal(xr * 2.0**23, np.round(xr * 2.0**23))
+    xs, ok, _ = O.step(inst, x, T=0, lr=0.1, seed=7, epoch=3, b_offset=100, restart=True)
+    assert not ok.any()
+    assert np.array_equal(xr, xs)
+    with pytest.raises(ValueError):
+        O.rephase(x, 3)
+
+
 def test_local_optimum_example_gradient():
     g = golden("local_example.txt")
     inst = gen.from_lists(4, [(gen.XOR, 1, [1, 2]), (gen.XOR, 1, [2, 3]), (gen.XOR, 1, [3, 4])])
