@@ -459,6 +459,95 @@ void fill_weights(ffsat_instance *I) {
     }
 }
 
+// Literal placement of one product-path warp task (32 lanes; segment j of the
+// task owns lanes [j G, j G + G), each lane kProdR slots starting at the
+// segment's offset).  Position r of every lane is one gather and one
+// scatter-add instruction of the warp, so we fill the task position by
+// position with a maximum bipartite matching of lanes to shared-memory banks
+// (bank = variable mod 32): a lane may take any literal still left in its
+// segment (the product is order-free), a segment places at least as many
+// literals at each position as its remaining slots require, and lanes that
+// need not place a literal get the padding literal.  Literals that cannot be
+// placed without a conflict are placed anyway.
+void bank_place_products(std::vector<int32_t> &lits, const std::vector<int4> &meta, int4 task, int32_t pad) {
+    constexpr int RL = kProdR;
+    const int G = (task.x >> 8) & 0xff;
+    const int nseg = task.z;
+    const int lanes = nseg * G;
+    std::vector<std::vector<int32_t>> pool(nseg);
+    std::vector<int32_t> base(nseg);
+    for (int j = 0; j < nseg; ++j) {
+        const int4 m = meta[task.y + j];
+        base[j] = m.x;
+        for (int t = 0; t < G * RL; ++t) {
+            const int32_t l = lits[(size_t)m.x + t];
+            if (l != pad) pool[j].push_back(l);
+        }
+    }
+    std::vector<int32_t> out((size_t)lanes * RL, pad);
+    for (int r = 0; r < RL; ++r) {
+        int owner[32];
+        std::fill(owner, owner + 32, -1);
+        std::vector<int32_t> pick(lanes, -1);  // index into the segment's pool
+        std::function<bool(int, uint32_t &)> augment = [&](int l, uint32_t &seen) -> bool {
+            const auto &P = pool[l / G];
+            for (size_t t = 0; t < P.size(); ++t) {
+                const int bk = (int)((uint32_t)P[t] & 31u);
+                if (seen & (1u << bk)) continue;
+                seen |= 1u << bk;
+                if (owner[bk] < 0 || augment(owner[bk], seen)) {
+                    owner[bk] = l;
+                    pick[l] = (int32_t)t;
+                    return true;
+                }
+            }
+            return false;
+        };
+        // lanes that must place a literal first, then the optional ones
+        std::vector<int> need(nseg);
+        for (int j = 0; j < nseg; ++j) need[j] = std::max(0, (int)pool[j].size() - G * (RL - 1 - r));
+        for (int pass = 0; pass < 2; ++pass)
+            for (int l = 0; l < lanes; ++l) {
+                const int j = l / G, sl = l % G;
+                const bool required = sl < need[j];
+                if (required != (pass == 0) || pool[j].empty() || sl >= (int)pool[j].size()) continue;
+                uint32_t seen = 0;
+                augment(l, seen);
+            }
+        // take the matched literals out of the pools (largest pool index first per segment)
+        std::vector<std::vector<std::pair<int32_t, int>>> taken(nseg);
+        for (int bk = 0; bk < 32; ++bk)
+            if (owner[bk] >= 0) taken[owner[bk] / G].push_back({pick[owner[bk]], owner[bk]});
+        for (int j = 0; j < nseg; ++j) {
+            auto &T = taken[j];
+            std::sort(T.begin(), T.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+            for (const auto &pr : T) {
+                out[(size_t)pr.second * RL + r] = pool[j][pr.first];
+                pool[j].erase(pool[j].begin() + pr.first);
+            }
+            // required lanes left unmatched take the literal whose bank is least used
+            int placed = (int)T.size();
+            for (int sl = 0; sl < G && placed < need[j]; ++sl) {
+                const int l = j * G + sl;
+                if (out[(size_t)l * RL + r] != pad || pool[j].empty()) continue;
+                int load[32] = {0};
+                for (int ll = 0; ll < lanes; ++ll) {
+                    const int32_t v = out[(size_t)ll * RL + r];
+                    if (v != pad) load[(uint32_t)v & 31u]++;
+                }
+                size_t best = 0;
+                for (size_t t = 1; t < pool[j].size(); ++t)
+                    if (load[(uint32_t)pool[j][t] & 31u] < load[(uint32_t)pool[j][best] & 31u]) best = t;
+                out[(size_t)l * RL + r] = pool[j][best];
+                pool[j].erase(pool[j].begin() + best);
+                ++placed;
+            }
+        }
+    }
+    for (int j = 0; j < nseg; ++j)
+        std::memcpy(lits.data() + base[j], out.data() + (size_t)j * G * RL, (size_t)G * RL * sizeof(int32_t));
+}
+
 // Image k = {tasks | clauses | segmeta | segment literals}, each part 16-byte
 // aligned.  Segment s of length L on lanes G = seg_lanes(L, R) occupies G * R
 // literal slots; lane sl reads slots [sl R, sl R + R).  Unused slots hold the
@@ -478,6 +567,8 @@ void build_image(ffsat_instance *I, int k) {
         lits.resize((size_t)off + (size_t)G * R, pad);
         meta[s] = make_int4(off, si.y, si.z, si.w);
     }
+    for (const int4 &t : I->tasks[k])
+        if ((t.x & 0xff) == TASK_PROD) bank_place_products(lits, meta, t, I->n);
     std::vector<int4> &img = I->image[k];
     img.clear();
     I->img_off[k][0] = (int32_t)img.size();
