@@ -328,7 +328,26 @@ void build_table(int type, int param, int L, int form, std::vector<float> &tf, s
 // Warp tasks for one node R: node tasks (longest first), then product tasks,
 // then clause tasks.  Segments are node constraints followed by product
 // constraints, each group sorted by length, descending.
-void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clause, int node_r, TaskSet &ts) {
+// Clause groups (32 clauses) per clause task for a kernel with `warps` warps:
+// the choice that minimises (rounds of tasks over the warps) x (task length),
+// counting one group per clause task step plus a fixed task overhead and each
+// other task as one group.
+int clause_groups_per_task(int groups, int other_tasks, int warps) {
+    double best = 1e300;
+    int pick = kClausePerLane;
+    for (int k = kClausePerLane; k >= 1; k >>= 1) {
+        const int tasks = (groups + k - 1) / k + other_tasks;
+        const double t = (double)((tasks + warps - 1) / warps) * (k + 0.3);
+        if (t < best - 1e-9) {
+            best = t;
+            pick = k;
+        }
+    }
+    return pick;
+}
+
+void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clause, int node_r, int warps,
+                 TaskSet &ts) {
     ts.tasks.clear();
     ts.node_r = node_r;
     auto group = [&](int first, int count, int kind, int R) {
@@ -353,8 +372,13 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
     };
     if (n_node_seg > 0) group(0, n_node_seg, TASK_NODE, node_r);
     group(n_node_seg, (int)seg_len.size() - n_node_seg, TASK_PROD, kProdR);
-    const int per = 32 * kClausePerLane;  // the clause list is padded to a multiple of this
-    for (int c = 0; c < n_clause; c += per) ts.tasks.push_back(make_int4(TASK_CLAUSE, c, per, 0));
+    // the clause list is padded to whole groups of 32; a task covers 1..kClausePerLane groups
+    // (1, 2 or 4 groups: the kernel has one unrolled body for each; a tail that is not
+    // a whole task is split into smaller powers of two)
+    const int k = clause_groups_per_task(n_clause / 32, (int)ts.tasks.size(), warps);
+    int c = 0;
+    for (int kk = k; kk >= 1; kk >>= 1)
+        for (; c + 32 * kk <= n_clause; c += 32 * kk) ts.tasks.push_back(make_int4(TASK_CLAUSE, c, 32 * kk, 0));
 }
 
 int smem_mode_for(int n, size_t elem, size_t image_bytes, int max_smem, size_t &bytes) {
@@ -930,8 +954,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
         P->clauses[k] = make_int4(l3[0], l3[1], l3[2], 0);
     }
     bank_order(P->clauses, clause_ids);
-    const size_t per_task = 32 * kClausePerLane;
-    const size_t n_clause_pad = (clause_ids.size() + per_task - 1) / per_task * per_task;
+    const size_t n_clause_pad = (clause_ids.size() + 31) / 32 * 32;
     P->clauses.resize(n_clause_pad, make_int4(n_vars, n_vars, n_vars, 0));
     P->clause_wd.assign(n_clause_pad, 0.0);
     for (size_t k = 0; k < clause_ids.size(); ++k) P->slot[clause_ids[k]] = (int32_t)k;
@@ -956,8 +979,8 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     P->nr[0] = nr32;
     P->nr[1] = nr64;
     TaskSet ts32, ts64;
-    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, nr32, ts32);
-    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, nr64, ts64);
+    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, nr32, fused_threads(false, nr32) / 32, ts32);
+    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, nr64, fused_threads(true, nr64) / 32, ts64);
     P->tasks[0] = ts32.tasks;
     P->tasks[1] = ts64.tasks;
     build_image(P, 0);
@@ -966,11 +989,21 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     const bool tune = opt.autotune && !node_c.empty() && opt.node_r == 0 && max_node_len <= 8 * 32;
     if (tune) {
         TaskSet ts8;
-        build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, 8, ts8);
+        build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, 8, fused_threads(false, 8) / 32, ts8);
         P->n_images = 3;
         P->nr[2] = 8;
         P->tasks[2] = ts8.tasks;
         build_image(P, 2);
+    }
+    // every literal the kernels will index must name a variable or one of the two dummies
+    for (int k = 0; k < P->n_images; ++k) {
+        const int32_t *w = reinterpret_cast<const int32_t *>(P->image[k].data());
+        for (size_t i = (size_t)P->img_off[k][1] * 4; i < (size_t)P->img_off[k][2] * 4; ++i)
+            if ((i & 3) != 3 && ((uint32_t)w[i] & 0x7fffffffu) > (uint32_t)n_vars + 1)
+                return fail(FFSAT_ERR_PARAM, "internal: clause record %zu out of range", i / 4);
+        for (size_t i = (size_t)P->img_off[k][3] * 4; i < P->image[k].size() * 4; ++i)
+            if (((uint32_t)w[i] & 0x7fffffffu) > (uint32_t)n_vars + 1)
+                return fail(FFSAT_ERR_PARAM, "internal: segment literal %zu out of range", i);
     }
 
     // ---- device ----

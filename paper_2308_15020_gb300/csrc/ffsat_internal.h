@@ -13,7 +13,8 @@ namespace ffsat {
 
 // Literals per lane on the product (closed-form) path.
 constexpr int kProdR = 8;
-// Clauses per lane in one clause task.
+// Largest number of clauses per lane in one clause task (groups of 32 clauses;
+// the host picks 1, 2 or 4 per instance and kernel width).
 constexpr int kClausePerLane = 4;
 // Packed literal: (variable << 1) | negated.  Padding literal: -1.
 constexpr int32_t kPadLit = -1;

@@ -199,19 +199,19 @@ __device__ __forceinline__ void load_lits(const int32_t *p, uint32_t (&lp)[RL]) 
 }
 
 // ---------------------------------------------------------------------------
-// clause3 path: 32 * kClausePerLane clauses per task (the list is padded)
+// clause3 path: task.z = 32 CPL clauses, CPL in {1, 2, 4} (whole groups of 32)
 // ---------------------------------------------------------------------------
 // FE = 2 w q0 q1 q2 - w; the constant -w is folded into f_const on the host,
 // so facc collects 2 w q0 q1 q2 only.
-template <typename R, int XG, typename Acc>
+template <typename R, int XG, int CPL, typename Acc>
 __device__ __forceinline__ void clause_task(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
                                             const Acc &acc, bool want_g, R &facc) {
     const int n = V.n;
-    int4 cl[kClausePerLane];
+    int4 cl[CPL];
 #pragma unroll
-    for (int k = 0; k < kClausePerLane; ++k) cl[k] = S.clauses[task.y + k * 32 + lane];
+    for (int k = 0; k < CPL; ++k) cl[k] = S.clauses[task.y + k * 32 + lane];
 #pragma unroll
-    for (int k = 0; k < kClausePerLane; ++k) {
+    for (int k = 0; k < CPL; ++k) {
         const R w = clause_weight<R>(V, cl[k], task.y + k * 32 + lane);
         const R y0 = gather<R, XG>(xrow, (uint32_t)cl[k].x, n);
         const R y1 = gather<R, XG>(xrow, (uint32_t)cl[k].y, n);
@@ -594,7 +594,12 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
             const int4 task = S.tasks[t];
             const int kind = task.x & 0xff;
             if (kind == TASK_CLAUSE) {
-                clause_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
+                if (task.z == 128)
+                    clause_task<R, XG, 4>(V, S, task, lane, xrow, G, want_g, facc);
+                else if (task.z == 64)
+                    clause_task<R, XG, 2>(V, S, task, lane, xrow, G, want_g, facc);
+                else
+                    clause_task<R, XG, 1>(V, S, task, lane, xrow, G, want_g, facc);
             } else if (kind == TASK_PROD) {
                 prod_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
             } else {

@@ -1,6 +1,7 @@
 """Multi-rank host logic on CPU (gloo, world size 2): points sharded across
 ranks with their global index as restart key give the same rounds as one
-process, the solved flags combine with an OR, and the step time reduces with MAX."""
+process, the solved flags combine with an OR, the step time reduces with MAX,
+and the ERWA counts summed over ranks give the single-process weights."""
 import os
 import socket
 
@@ -63,3 +64,58 @@ def test_sharded_rounds_equal_single_process():
     assert np.array_equal(got, want)
     assert any_solved == int(solved.any())
     assert tmax == 2.0
+
+
+def _erwa_worker(rank, world, port, out):
+    from paper_2308_15020_gb300 import shard
+
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    inst = gen.cnf_xor_2000(3, n=300)
+    B = 13  # uneven split
+    off, nb = shard.shard(B, rank, world)
+    x_all = gen.uniform_points(B, inst.n, 21, dtype=np.float64)
+    w = np.asarray(inst.weights, dtype=np.float64)
+    for r in range(3):
+        x1, solved, _ = O.step(inst, x_all[off:off + nb], T=5, lr=0.1, seed=4, epoch=r, b_offset=off, restart=False,
+                               nthreads=1, weights=w)
+        U = torch.from_numpy(O.unsat_counts(inst, x1))
+        any_solved = shard.combine_round(torch.from_numpy(solved), U)
+        w = O.erwa(U.numpy(), w, 0.4)
+        x_all[off:off + nb] = O.rephase(x1, 2 if r % 2 == 0 else 1, solved, seed=4, epoch=100 + r, b_offset=off)
+    xs = [torch.zeros(B, inst.n, dtype=torch.float64) for _ in range(world)]
+    dist.all_gather(xs, torch.from_numpy(x_all))
+    if rank == 0:
+        out.put((w, any_solved, [s.numpy() for s in xs]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_sharded_erwa_equals_single_process():
+    from paper_2308_15020_gb300 import shard
+
+    world = 2
+    assert [shard.shard(13, r, 2) for r in range(2)] == [(0, 7), (7, 6)]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_erwa_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    w_got, any_solved, xs = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    # the same three rounds in one process over all 13 points
+    inst = gen.cnf_xor_2000(3, n=300)
+    x = gen.uniform_points(13, inst.n, 21, dtype=np.float64)
+    w = np.asarray(inst.weights, dtype=np.float64)
+    for r in range(3):
+        x1, solved, _ = O.step(inst, x, T=5, lr=0.1, seed=4, epoch=r, restart=False, nthreads=1, weights=w)
+        w = O.erwa(O.unsat_counts(inst, x1), w, 0.4)
+        x = O.rephase(x1, 2 if r % 2 == 0 else 1, solved, seed=4, epoch=100 + r)
+    assert np.array_equal(w_got, w)
+    assert any_solved == bool(solved.any())
+    got = np.concatenate([xs[0][:7], xs[1][7:]])
+    assert np.array_equal(got, x)
