@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import math
 import json
 import os
 import statistics
@@ -328,6 +329,127 @@ def run_reference(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------------------------------------
+# time-to-SAT lines (configuration 1: random 3-SAT n=100; configuration 5: learned restarts)
+# ---------------------------------------------------------------------------------------------
+
+TTS_SEEDS = 20          # satisfiable seeds of the n=100 workload (decided by DPLL)
+TTS_MAX_ROUNDS = 200    # CLS rounds of T iterations before a run counts as unsolved
+
+
+def oracle_time_to_sat(inst, cfg, seed: int):
+    """The same CLS as the GPU run (FP64 PGD rounds, ERWA weights, rephasing
+    policy) composed from the oracle's functions on the host cores."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    phase = {"O": 0, "F": 1, "R": 2}
+    t0 = time.perf_counter()
+    x = O.rephase(np.zeros((cfg.B, inst.n)), 2, None, seed=seed, epoch=0)
+    w = np.asarray(inst.weights, dtype=np.float64).copy()
+    for r in range(cfg.max_rounds):
+        x, solved, _ = O.step(inst, x, T=cfg.T, lr=cfg.lr, seed=seed, epoch=r + 1, restart=False, weights=w)
+        if solved.any():
+            return True, time.perf_counter() - t0, r + 1
+        if cfg.heuristics:
+            w = O.erwa(O.unsat_counts(inst, x), w, cfg.alpha)
+            ph = phase[cfg.policy[r % len(cfg.policy)]]
+        else:
+            ph = 2
+        x = O.rephase(x, ph, solved, seed=seed, epoch=r + 1)
+    return False, time.perf_counter() - t0, cfg.max_rounds
+
+
+def run_tts_3sat(args, rank: int, world: int, local_rank: int):
+    """Median time-to-SAT over satisfiable seeds of the random 3-SAT n=100
+    workload: FP64 points, B=32, T=200, lr=0.1, ERWA + (ROF) rephasing."""
+    import torch
+
+    from paper_2308_15020_gb300 import ffsat, learned
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    cfg = learned.CLSConfig(B=32, T=200, lr=0.1, max_rounds=TTS_MAX_ROUNDS, seed=11, heuristics=True,
+                            policy="ROF", dtype="f64")
+    t_sel = time.perf_counter()
+    chosen = gen.satisfiable_3sat_100(TTS_SEEDS, 0)
+    t_sel = time.perf_counter() - t_sel
+    runs, e2e, launches = [], [], 0
+    clocks = ClockSampler(visible_device_index(local_rank))
+    clocks.start()
+    for k, (s_, inst) in enumerate(chosen):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        h = ffsat.Instance(inst)
+        t_load = time.perf_counter() - t0
+        learned.warm(h, inst.n, cfg, None)
+        r = learned.time_to_sat(h, inst.n, cfg, cfg.seed + 7919 * k, None)
+        runs.append(r)
+        e2e.append(t_load + r.seconds)
+        launches += 5 * r.rounds  # per round: the step, the three ERWA kernels, the rephase
+    clk = clocks.stop()
+    budget = max([r.seconds for r in runs if not r.solved] or [0.0])
+    par2 = [r.seconds if r.solved else 2 * max(budget, 1e-9) for r in runs]
+    cpu = None
+    if not args.no_cpu_baseline:
+        sys.path.insert(0, os.path.join(ROOT, "oracle"))
+        import oracle as O
+
+        ct, spent, used = [], 0.0, 0
+        for k, (s_, inst) in enumerate(chosen):
+            ok, dt, rounds = oracle_time_to_sat(inst, cfg, cfg.seed + 7919 * k)
+            ct.append(dt if ok else math.inf)
+            spent += dt
+            used += 1
+            if spent > args.cpu_seconds:
+                break
+        cpu = {"value": float(np.median(ct)), "unit": "s", "cores": O.max_threads(), "kind": "oracle",
+               "sample": f"the same CLS (FP64 oracle PGD rounds, ERWA, ROF) on the first {used} of the "
+                         f"{len(chosen)} seeds, median over those, {spent:.1f} s"}
+    line = {
+        "metric": "time-to-SAT (median s over satisfiable seeds, PAR-2 for unsolved)", "value": float(np.median(par2)),
+        "unit": "s", "n_gpus": 1, "steps": len(chosen), "warmup": 1, "ms_per_step": 1e3 * float(np.mean(par2)),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generator; satisfiability of each seed decided by DPLL)",
+        "config": {"workload": "3sat_n100_tts", "n": 100, "m": 426, "B": cfg.B, "pgd_iters_per_round": cfg.T,
+                   "lr": cfg.lr, "max_rounds": cfg.max_rounds, "heuristics": "ERWA alpha 0.4 + (ROF) rephasing",
+                   "seeds": [s_ for s_, _ in chosen], "dpll_selection_s": t_sel},
+        "solved": sum(r.solved for r in runs), "median_rounds": float(np.median([r.rounds for r in runs])),
+        "roofline": None, "cpu_baseline": cpu,
+        "e2e": {"value": float(np.median(e2e)), "unit": "s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "note": "instance load (host preprocessing and upload) plus the solve"},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_learned(args, rank: int, world: int, local_rank: int):
+    """Configuration 5: the restart-proposal network trained on CLS best points of
+    planted CNF-XOR n=2000 instances, A/B time-to-SAT on held-out n=5000 ones."""
+    import torch
+
+    from paper_2308_15020_gb300 import learned
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    t0 = time.perf_counter()
+    res = learned.learned_restart_experiment(train_count=args.train_count, test_count=args.test_count)
+    line = {
+        "metric": "time-to-SAT (median s, PAR-2), learned vs uniform restarts", "value": res["median_par2_s"]["learned"],
+        "unit": "s", "n_gpus": 1, "steps": res["test_instances"], "warmup": 0,
+        "ms_per_step": 1e3 * (time.perf_counter() - t0) / max(1, res["test_instances"]),
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32 CLS / bf16 network",
+        "data": "synthetic planted instances (seeded generator)",
+        "config": {"workload": "learned_restart", "train": f"{res['train_instances']} x n={res['n_train']}",
+                   "test": f"{res['test_instances']} x n={res['n_test']}"},
+        "uniform_par2_s": res["median_par2_s"]["uniform"], "experiment": res,
+        "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------------------------
 # GPU leg
 # ---------------------------------------------------------------------------------------------
 
@@ -614,7 +736,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cnf_xor_n2000", choices=list(WORKLOADS))
+    ap.add_argument("--workload", default="cnf_xor_n2000",
+                    choices=list(WORKLOADS) + ["3sat_n100_tts", "learned_restart"])
+    ap.add_argument("--train-count", type=int, default=2000, help="learned_restart: training instances")
+    ap.add_argument("--test-count", type=int, default=100, help="learned_restart: held-out instances")
     ap.add_argument("--T", type=int, default=0, help="PGD iterations per step (0 = workload default)")
     ap.add_argument("--B", type=int, default=0, help="restart points per GPU (0 = workload default)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -626,8 +751,16 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.impl == "reference":
+    if args.workload in ("3sat_n100_tts", "learned_restart") and args.impl == "reference":
+        if rank == 0:
+            print(json.dumps({"impl": "reference", "unavailable": "time-to-SAT lines time the oracle's CLS inside "
+                              "the GPU run (cpu_baseline); use --workload 3sat_n100 for the oracle's rate"}))
+    elif args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "3sat_n100_tts":
+        run_tts_3sat(args, rank, world, local_rank)
+    elif args.workload == "learned_restart":
+        run_learned(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

@@ -354,3 +354,108 @@ def dyadic_points(B: int, n: int, seed: int = 0, bits: int = 6, dtype=np.float64
     rng = _rng(seed, 14)
     k = rng.integers(-(1 << bits), (1 << bits) + 1, size=(B, n))
     return (k / float(1 << bits)).astype(dtype)
+
+
+def dpll_model(inst: Instance, max_nodes: int = 2_000_000) -> Optional[np.ndarray]:
+    """A model of a pure CNF instance found by DPLL (unit propagation, branching
+    on the variable with the largest Jeroslow-Wang score), or None when the
+    formula is unsatisfiable.  Selects satisfiable seeds of the random 3-SAT
+    workload; raises RuntimeError past max_nodes search nodes.  Models use the
+    paper's encoding: -1 True, +1 False."""
+    if np.any(inst.ctype != OR):
+        raise ValueError("dpll_model takes clauses only")
+    n = inst.n
+    clauses = [list(inst.lits[inst.row_ptr[c]:inst.row_ptr[c + 1]]) for c in range(inst.m)]
+    occ = [[] for _ in range(2 * n + 2)]  # literal -> clauses containing it
+    for ci, cl in enumerate(clauses):
+        for l in cl:
+            occ[l + n].append(ci)
+    val = [0] * (n + 1)  # 0 unassigned, +1 True, -1 False (literal l is true iff val[|l|] * sign(l) > 0)
+    nodes = [0]
+
+    def lit_val(l):
+        v = val[abs(l)]
+        return 0 if v == 0 else (1 if (v > 0) == (l > 0) else -1)
+
+    def propagate(trail):
+        changed = True
+        while changed:
+            changed = False
+            for cl in clauses:
+                free, sat = None, False
+                nfree = 0
+                for l in cl:
+                    s = lit_val(l)
+                    if s > 0:
+                        sat = True
+                        break
+                    if s == 0:
+                        nfree += 1
+                        free = l
+                if sat:
+                    continue
+                if nfree == 0:
+                    return False
+                if nfree == 1:
+                    val[abs(free)] = 1 if free > 0 else -1
+                    trail.append(abs(free))
+                    changed = True
+        return True
+
+    def pick():
+        score = {}
+        for cl in clauses:
+            if any(lit_val(l) > 0 for l in cl):
+                continue
+            free = [l for l in cl if lit_val(l) == 0]
+            w = 2.0 ** -len(free)
+            for l in free:
+                score[l] = score.get(l, 0.0) + w
+        if not score:
+            return None
+        return max(score.items(), key=lambda kv: kv[1])[0]
+
+    def solve():
+        nodes[0] += 1
+        if nodes[0] > max_nodes:
+            raise RuntimeError("dpll_model: node budget exceeded")
+        trail = []
+        if not propagate(trail):
+            for v in trail:
+                val[v] = 0
+            return False
+        l = pick()
+        if l is None:
+            return True
+        for choice in (l, -l):
+            val[abs(choice)] = 1 if choice > 0 else -1
+            if solve():
+                return True
+            val[abs(choice)] = 0
+        for v in trail:
+            val[v] = 0
+        return False
+
+    import sys
+    old = sys.getrecursionlimit()
+    sys.setrecursionlimit(max(old, 10 * n + 100))
+    try:
+        ok = solve()
+    finally:
+        sys.setrecursionlimit(old)
+    if not ok:
+        return None
+    return np.array([-1 if val[v] > 0 else 1 for v in range(1, n + 1)], dtype=np.int8)
+
+
+def satisfiable_3sat_100(count: int, seed0: int = 0):
+    """The first `count` seeds >= seed0 whose uniform random 3-SAT n=100, m=426
+    instance is satisfiable (decided by dpll_model), with the instances."""
+    out = []
+    s = seed0
+    while len(out) < count:
+        inst = uniform_3sat_100(s)
+        if dpll_model(inst) is not None:
+            out.append((s, inst))
+        s += 1
+    return out

@@ -28,6 +28,7 @@ class CLSConfig:
     heuristics: bool = True  # ERWA weights + rephasing between rounds (else plain restarts)
     alpha: float = 0.4       # ERWA decay (Prop. "Adaptive weight")
     policy: str = "ROF"      # rephasing policy, repeated: R random, O original, F flipped
+    dtype: str = "f32"       # real type of the points: "f32" or "f64"
 
 
 _PHASE = {"O": 0, "F": 1, "R": 2}
@@ -43,7 +44,7 @@ class _Search:
         import torch
 
         self.h, self.cfg, self.seed, self.prop = h, cfg, seed, prop
-        self.x = torch.zeros(cfg.B, n, dtype=torch.float32, device="cuda")
+        self.x = torch.zeros(cfg.B, n, dtype=torch.float64 if cfg.dtype == "f64" else torch.float32, device="cuda")
         self.U = torch.zeros(h.m, dtype=torch.int32, device="cuda") if cfg.heuristics else None
         if prop is None:
             h.rephase(self.x, ffsat.FFSAT_PHASE_RANDOM, seed=seed, epoch=0)
@@ -148,6 +149,7 @@ class SatRun:
     solved: bool
     seconds: float
     rounds: int
+    best_unsat: int = -1  # fewest violated constraints of any point seen (0 when solved)
 
 
 def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optional[ffsat.MPNN] = None) -> SatRun:
@@ -161,13 +163,16 @@ def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optio
     t0 = time.perf_counter()
     prop = None if net is None else net.forward(h)
     S = _Search(h, n, cfg, seed, prop)
+    best = None
     for r in range(cfg.max_rounds):
-        solved, _ = S.round(r)
+        solved, nun = S.round(r)
+        m = nun.min()
+        best = m if best is None else torch.minimum(best, m)
         if bool(solved.any().item()):
             torch.cuda.synchronize()
-            return SatRun(True, time.perf_counter() - t0, r + 1)
+            return SatRun(True, time.perf_counter() - t0, r + 1, 0)
     torch.cuda.synchronize()
-    return SatRun(False, time.perf_counter() - t0, cfg.max_rounds)
+    return SatRun(False, time.perf_counter() - t0, cfg.max_rounds, int(best.item()) if best is not None else -1)
 
 
 @dataclass
@@ -180,15 +185,36 @@ class ABResult:
         v = [r.seconds if r.solved else math.inf for r in runs]
         return float(np.median(v)) if v else math.nan
 
+    @staticmethod
+    def _par2(runs, budget):
+        """Median PAR-2 time: unsolved runs count as twice the budget (the paper's
+        convention for unsolved instances)."""
+        v = [r.seconds if r.solved else 2.0 * budget for r in runs]
+        return float(np.median(v)) if v else math.nan
+
     def summary(self):
+        budget = max([r.seconds for r in self.uniform + self.learned if not r.solved] or [0.0])
+        arms = {"uniform": self.uniform, "learned": self.learned}
         return {
             "instances": len(self.uniform),
-            "median_time_to_sat_s": {"uniform": self._median(self.uniform), "learned": self._median(self.learned)},
-            "median_rounds": {"uniform": float(np.median([r.rounds for r in self.uniform])),
-                              "learned": float(np.median([r.rounds for r in self.learned]))},
-            "solved": {"uniform": sum(r.solved for r in self.uniform),
-                       "learned": sum(r.solved for r in self.learned)},
+            "median_time_to_sat_s": {k: self._median(v) for k, v in arms.items()},
+            "median_par2_s": {k: self._par2(v, budget) for k, v in arms.items()},
+            "par2_budget_s": budget,
+            "median_rounds": {k: float(np.median([r.rounds for r in v])) for k, v in arms.items()},
+            "solved": {k: sum(r.solved for r in v) for k, v in arms.items()},
+            "mean_best_unsat": {k: float(np.mean([r.best_unsat for r in v])) for k, v in arms.items()},
         }
+
+
+def warm(h: ffsat.Instance, n: int, cfg: CLSConfig, net: Optional[ffsat.MPNN]):
+    """Untimed first use of an instance: kernel limits, scratch, the network's graph data."""
+    import torch
+
+    x = torch.zeros(cfg.B, n, dtype=torch.float64 if cfg.dtype == "f64" else torch.float32, device="cuda")
+    h.step(x, T=1, lr=cfg.lr, restart=False)
+    if net is not None:
+        net.forward(h)
+    torch.cuda.synchronize()
 
 
 def ab_test(net: ffsat.MPNN, instances, cfg: CLSConfig) -> ABResult:
@@ -197,7 +223,7 @@ def ab_test(net: ffsat.MPNN, instances, cfg: CLSConfig) -> ABResult:
     for k, inst in enumerate(instances):
         h = ffsat.Instance(inst)
         seed = cfg.seed + 7919 * k
-        time_to_sat(h, inst.n, cfg, seed, None)  # warm the instance's kernels and graph data
+        warm(h, inst.n, cfg, net)
         res.uniform.append(time_to_sat(h, inst.n, cfg, seed, None))
         res.learned.append(time_to_sat(h, inst.n, cfg, seed, net))
     return res
@@ -222,3 +248,36 @@ def planted_3sat_family(count: int, n: int, seed0: int, ratio: float = 4.2):
     """Planted random 3-SAT at the given clause ratio."""
     return [gen.random_ksat(n, int(round(ratio * n)), 3, seed0 + i, planted=gen.planted_assignment(n, seed0 + i))
             for i in range(count)]
+
+
+def learned_restart_experiment(train_count: int = 2000, test_count: int = 100, n_train: int = 2000,
+                               n_test: int = 5000, family: str = "cnf_xor", self_train_rounds: int = 2,
+                               epochs: int = 6, collect_cfg: Optional[CLSConfig] = None,
+                               test_cfg: Optional[CLSConfig] = None, seed: int = 0, log=None):
+    """Train the proposal network on the CLS's own best points over train_count
+    seeded planted instances of the family at n_train, then A/B time-to-SAT on
+    test_count held-out instances at n_test (uniform restarts vs restarts around
+    the proposal, same seeds, same heuristics).  Returns a summary dict."""
+    def say(*a):
+        if log is not None:
+            log(*a)
+
+    make = planted_family if family == "cnf_xor" else planted_3sat_family
+    collect_cfg = collect_cfg or CLSConfig(B=64, T=100, lr=0.1, max_rounds=10, seed=3)
+    test_cfg = test_cfg or CLSConfig(B=256, T=100, lr=0.1, max_rounds=30, seed=9)
+    t0 = time.perf_counter()
+    train_set = make(train_count, n_train, 100000 + seed)
+    net = ffsat.MPNN(3, seed + 7)
+    hist, losses = self_train(net, train_set, collect_cfg, rounds=self_train_rounds, epochs=epochs)
+    t_train = time.perf_counter() - t0
+    say(f"trained on {train_count} instances in {t_train:.0f} s; target #unsat per round {hist}")
+    test_set = make(test_count, n_test, 900000 + seed)
+    agree = sign_agreement(net, test_set)
+    res = ab_test(net, test_set, test_cfg)
+    out = res.summary()
+    out.update({"family": family, "train_instances": train_count, "n_train": n_train, "test_instances": test_count,
+                "n_test": n_test, "target_mean_unsat_per_self_training_round": hist,
+                "final_train_loss": losses[-1] if losses else None, "held_out_sign_agreement": agree,
+                "train_seconds": t_train, "total_seconds": time.perf_counter() - t0,
+                "collect": vars(collect_cfg), "test": vars(test_cfg)})
+    return out
