@@ -395,17 +395,20 @@ def run_tts_3sat(args, rank: int, world: int, local_rank: int):
         sys.path.insert(0, os.path.join(ROOT, "oracle"))
         import oracle as O
 
-        ct, spent, used = [], 0.0, 0
+        ct, spent, used, nsolved = [], 0.0, 0, 0
         for k, (s_, inst) in enumerate(chosen):
             ok, dt, rounds = oracle_time_to_sat(inst, cfg, cfg.seed + 7919 * k)
-            ct.append(dt if ok else math.inf)
+            ct.append((ok, dt))
+            nsolved += ok
             spent += dt
             used += 1
             if spent > args.cpu_seconds:
                 break
-        cpu = {"value": float(np.median(ct)), "unit": "s", "cores": O.max_threads(), "kind": "oracle",
+        cbudget = max([dt for ok, dt in ct if not ok] or [0.0])
+        cpar2 = [dt if ok else 2 * max(cbudget, 1e-9) for ok, dt in ct]
+        cpu = {"value": float(np.median(cpar2)), "unit": "s", "cores": O.max_threads(), "kind": "oracle",
                "sample": f"the same CLS (FP64 oracle PGD rounds, ERWA, ROF) on the first {used} of the "
-                         f"{len(chosen)} seeds, median over those, {spent:.1f} s"}
+                         f"{len(chosen)} seeds, median PAR-2 over those ({nsolved} solved), {spent:.1f} s"}
     line = {
         "metric": "time-to-SAT (median s over satisfiable seeds, PAR-2 for unsolved)", "value": float(np.median(par2)),
         "unit": "s", "n_gpus": 1, "steps": len(chosen), "warmup": 1, "ms_per_step": 1e3 * float(np.mean(par2)),

@@ -200,6 +200,44 @@ int ffsat_step_noalloc(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, 
 int ffsat_check(ffsat_instance *inst, int32_t B, const void *x, int32_t dtype, uint8_t *sat, int32_t *n_unsat,
                 void *stream);
 
+/* ---- projected gradient with line search (App. A.3, Alg. PGFP) ------------------------ */
+
+typedef struct ffsat_pgfp_args {
+    int32_t T;         /* at most T iterations per call (>= 0) */
+    int32_t restart;   /* 1: points whose sign vector is not a model restart uniformly */
+    double eta0;       /* initial step size of every point (> 0) */
+    double beta;       /* backtracking factor in (0, 1); 0.5 is usual */
+    int32_t maxls;     /* trial steps per iteration (>= 1); the last trial is taken when none passes */
+    int32_t pad;
+    double eta_min;    /* a point stops once its step size falls below this (the paper: 1e-12) */
+    double slack;      /* absolute slack (>= 0) of the sufficient-decrease test, for the rounding of F */
+    uint64_t seed;     /* restart seed, epoch and global index of point 0, as in ffsat_step_args */
+    uint64_t epoch;
+    uint64_t b_offset;
+    int32_t *unsat_counts; /* device int32 [n_cons] or NULL, as in ffsat_step_args */
+    int32_t *iters;    /* device int32 [B] or NULL: iterations each point took */
+    double *eta_out;   /* device double [B] or NULL: each point's final step size */
+} ffsat_pgfp_args;
+
+/* One CLS round with the paper's projected-gradient fixed-point update and a
+ * FISTA line search (App. A.3: "Default method ... is FISTA"; Beck and
+ * Teboulle's backtracking variant), per point, starting from x_0 = x[b]:
+ *   y_1 = x_0, t_1 = 1, eta = eta0;  for k = 1..T:
+ *     g = grad F(y_k);  eta <- eta * beta^i for the first i = 0, 1, .. (at most
+ *     maxls trials) with F(p) <= F(y_k) + <g, p - y_k> + |p - y_k|^2 / (2 eta) + slack,
+ *     p = clip(y_k - eta g, -1, 1);
+ *     x_k = p;  t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2;
+ *     y_{k+1} = clip(x_k + (t_k - 1) / t_{k+1} (x_k - x_{k-1}), -1, 1);
+ *     stop once eta < eta_min;
+ * then the exact check and the uniform restart as in ffsat_step, all in one
+ * launch.  The step size and the momentum start afresh in every call.
+ *   x: device [B, n] of dtype, updated in place;  solved, n_unsat: as in ffsat_step.
+ * Uses a per-instance [B, n] device scratch (allocated on first use or growth).
+ * Errors: FFSAT_ERR_ARG for bad parameters, or when the instance's x does not
+ * fit in shared memory (its shared-memory mode for dtype is 2). */
+int ffsat_step_pgfp(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, const ffsat_pgfp_args *args,
+                    uint8_t *solved, int32_t *n_unsat, void *stream);
+
 /* ---- restart heuristics (Sec. 5: weighting and rephasing) ---------------------------- */
 
 /* Rephasing phases (Sec. 5, "Rephasing Heuristics"). */

@@ -589,6 +589,88 @@ double orc_uniform(uint64_t seed, uint64_t epoch, uint64_t b, uint64_t v) {
     return ldexp((double)u, -23);
 }
 
+int orc_step_pgfp(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *lits,
+                  const uint8_t *type, const int32_t *param, const double *w,
+                  int32_t B, double *x, int32_t T, double eta0, double beta, int32_t maxls,
+                  double eta_min, double slack,
+                  uint64_t seed, uint64_t epoch, uint64_t b_offset, int restart,
+                  uint8_t *solved, int32_t *n_unsat, int32_t *iters, double *eta_out, int nthreads) {
+    if (!(eta0 > 0.0) || !(beta > 0.0 && beta < 1.0) || maxls < 1) return -1;
+    int nt = resolve_threads(nthreads);
+    int L = max_len(m, row_ptr);
+    int status = 0;
+#pragma omp parallel num_threads(nt)
+    {
+        double *ybuf = (double *)malloc(sizeof(double) * (size_t)(L + 1));
+        double *dy = (double *)malloc(sizeof(double) * (size_t)(L + 1));
+        size_t nn = (size_t)(n > 0 ? n : 1);
+        double *g = (double *)malloc(sizeof(double) * nn);
+        double *gp = (double *)malloc(sizeof(double) * nn);
+        double *yk = (double *)malloc(sizeof(double) * nn);   /* extrapolated point y_k */
+        double *pk = (double *)malloc(sizeof(double) * nn);   /* trial point p */
+#pragma omp for schedule(dynamic, 1)
+        for (int32_t b = 0; b < B; ++b) {
+            double *xb = x + (size_t)b * n; /* the iterate x_k (x_0 on entry) */
+            double eta = eta0, t = 1.0, fy, fp;
+            int rc = 0;
+            int32_t it = 0;
+            for (int32_t v = 0; v < n; ++v) yk[v] = xb[v];
+            while (it < T && rc == 0) {
+                ++it;
+                rc = eval_point(n, m, row_ptr, lits, type, param, w, yk, &fy, g, ybuf, dy, 0);
+                if (rc) break;
+                /* backtracking on the sufficient-decrease condition of the proximal
+                   (projected) gradient step */
+                for (int32_t ls = 0; ls < maxls; ++ls) {
+                    double d = 0.0, q = 0.0;
+                    for (int32_t v = 0; v < n; ++v) {
+                        double z = yk[v] - eta * g[v];
+                        z = z < -1.0 ? -1.0 : (z > 1.0 ? 1.0 : z);
+                        pk[v] = z;
+                        d += g[v] * (z - yk[v]);
+                        q += (z - yk[v]) * (z - yk[v]);
+                    }
+                    rc = eval_point(n, m, row_ptr, lits, type, param, w, pk, &fp, gp, ybuf, dy, 0);
+                    if (rc) break;
+                    if (fp <= fy + d + q / (2.0 * eta) + slack) break;
+                    if (ls + 1 < maxls) eta *= beta;
+                }
+                if (rc) break;
+                /* momentum: t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2, y = Pi(x_k + (t_k - 1)/t_{k+1} (x_k - x_{k-1})) */
+                double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+                double mom = (t - 1.0) / tn;
+                t = tn;
+                for (int32_t v = 0; v < n; ++v) {
+                    double xn = pk[v];
+                    double z = xn + mom * (xn - xb[v]);
+                    yk[v] = z < -1.0 ? -1.0 : (z > 1.0 ? 1.0 : z);
+                    xb[v] = xn;
+                }
+                if (eta < eta_min) break;
+            }
+            if (iters) iters[b] = it;
+            if (eta_out) eta_out[b] = eta;
+            int bad = rc != 0;
+            int32_t u = bad ? 0 : check_point(n, m, row_ptr, lits, type, param, xb, &bad);
+            n_unsat[b] = u;
+            solved[b] = (uint8_t)(!bad && u == 0);
+            if (bad) {
+#pragma omp atomic write
+                status = -1;
+            } else if (u != 0 && restart) {
+                for (int32_t v = 0; v < n; ++v) xb[v] = orc_uniform(seed, epoch, b_offset + (uint64_t)b, (uint64_t)v);
+            }
+        }
+        free(ybuf);
+        free(dy);
+        free(g);
+        free(gp);
+        free(yk);
+        free(pk);
+    }
+    return status;
+}
+
 int orc_rephase(int32_t n, int32_t B, double *x, int phase, const uint8_t *solved,
                 uint64_t seed, uint64_t epoch, uint64_t b_offset) {
     if (phase < 0 || phase > 2) return -1;

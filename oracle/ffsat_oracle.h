@@ -124,6 +124,28 @@ uint64_t orc_splitmix64(uint64_t state);
  * in both float and double. */
 double orc_uniform(uint64_t seed, uint64_t epoch, uint64_t b, uint64_t v);
 
+/* One outer round of Alg. 1 with the paper's projected-gradient fixed-point
+ * update (App. A.3, Alg. "PGFP") and a FISTA line search (Beck and Teboulle,
+ * backtracking variant), per point:
+ *   y_1 = x_0, t_1 = 1, eta = eta0; for k = 1..T:
+ *     g = grad F(y_k); find eta <- eta * beta^i (i >= 0, at most maxls trials,
+ *       the last trial accepted if none passes) with
+ *       F(p) <= F(y_k) + <g, p - y_k> + ||p - y_k||^2 / (2 eta) + slack,
+ *       p = clip(y_k - eta g, -1, 1);
+ *     x_k = p; t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2;
+ *     y_{k+1} = clip(x_k + (t_k - 1) / t_{k+1} (x_k - x_{k-1}), -1, 1);
+ *     stop once eta < eta_min (the paper's 1e-12).
+ * x holds x_0 on entry and the last iterate on return; then the exact check and
+ * the uniform restart as in orc_step.  iters[b] (optional) receives the
+ * iterations taken and eta_out[b] (optional) the final step size.  Returns 0,
+ * or -1 on bad input or parameters. */
+int orc_step_pgfp(int32_t n, int32_t m, const int64_t *row_ptr, const int32_t *lits,
+                  const uint8_t *type, const int32_t *param, const double *w,
+                  int32_t B, double *x, int32_t T, double eta0, double beta, int32_t maxls,
+                  double eta_min, double slack,
+                  uint64_t seed, uint64_t epoch, uint64_t b_offset, int restart,
+                  uint8_t *solved, int32_t *n_unsat, int32_t *iters, double *eta_out, int nthreads);
+
 /* Rephasing (Sec. "Rephasing Heuristics"): every point b with solved == NULL or
  * solved[b] == 0 takes phase 0 = original (x_b kept), 1 = flipped (x_b = -x_b)
  * or 2 = random (x_b[v] = orc_uniform(seed, epoch, b_offset + b, v)).

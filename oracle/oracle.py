@@ -57,6 +57,10 @@ def lib():
         L.orc_unsat_counts.restype = C.c_int
         L.orc_erwa.argtypes = [C.c_int32, _i32, C.c_double, _dp]
         L.orc_erwa.restype = None
+        L.orc_step_pgfp.argtypes = [C.c_int32, C.c_int32, _i64, _i32, _u8, _i32, _dp, C.c_int32, _dp, C.c_int32,
+                                    C.c_double, C.c_double, C.c_int32, C.c_double, C.c_double, C.c_uint64,
+                                    C.c_uint64, C.c_uint64, C.c_int, _u8, _i32, _i32, _dp, C.c_int]
+        L.orc_step_pgfp.restype = C.c_int
         L.orc_rephase.argtypes = [C.c_int32, C.c_int32, _dp, C.c_int, _u8, C.c_uint64, C.c_uint64, C.c_uint64]
         L.orc_rephase.restype = C.c_int
         L.orc_splitmix64.argtypes = [C.c_uint64]
@@ -233,6 +237,29 @@ def erwa(U, w, alpha: float = 0.4):
     w = _f64(w).copy()
     lib().orc_erwa(len(w), _p(U, _i32), alpha, _p(w, _dp))
     return w
+
+
+def step_pgfp(inst, x, T: int, eta0: float, beta: float = 0.5, maxls: int = 15, eta_min: float = 1e-12,
+              slack: float = 0.0, seed: int = 0, epoch: int = 0, b_offset: int = 0, restart: bool = True,
+              nthreads: int = 0, weights=None):
+    """One CLS round with the projected-gradient fixed-point update and FISTA
+    line search (App. A.3); returns (x_new, solved, n_unsat, iterations, eta)."""
+    rp, lits, ty, pa, w = _inst_arrays(inst)
+    if weights is not None:
+        w = _f64(weights)
+    x = _f64(np.atleast_2d(x)).copy()
+    B = x.shape[0]
+    solved = np.zeros(B, dtype=np.uint8)
+    nun = np.zeros(B, dtype=np.int32)
+    its = np.zeros(B, dtype=np.int32)
+    eta = np.zeros(B, dtype=np.float64)
+    rc = lib().orc_step_pgfp(inst.n, inst.m, _p(rp, _i64), _p(lits, _i32), _p(ty, _u8), _p(pa, _i32), _p(w, _dp), B,
+                             _p(x, _dp), T, eta0, beta, maxls, eta_min, slack, seed & 0xFFFFFFFFFFFFFFFF, epoch,
+                             b_offset, int(restart), _p(solved, _u8), _p(nun, _i32), _p(its, _i32), _p(eta, _dp),
+                             nthreads)
+    if rc != 0:
+        raise ValueError("oracle: bad input or parameters")
+    return x, solved, nun, its, eta
 
 
 def rephase(x, phase: int, solved=None, seed: int = 0, epoch: int = 0, b_offset: int = 0):

@@ -169,6 +169,8 @@ struct ffsat_instance {
     size_t smem32 = 0, smem64 = 0;
     void *d_scratch = nullptr;
     size_t scratch_bytes = 0;
+    void *d_yscratch = nullptr;  // extrapolated points of ffsat_step_pgfp
+    size_t yscratch_bytes = 0;
     ffsat_info info{};
     // learned-proposal graph data (built on first use)
     unsigned char *d_graph = nullptr;
@@ -1268,6 +1270,73 @@ int ffsat_step_noalloc(ffsat_instance *I, int32_t B, void *x, int32_t dtype, con
     return FFSAT_OK;
 }
 
+static int grow_scratch(void **p, size_t *have, size_t need) {
+    if (need <= *have) return FFSAT_OK;
+    if (*p) CUDA_TRY(cudaFree(*p));
+    *p = nullptr;
+    *have = 0;
+    CUDA_TRY(cudaMalloc(p, need));
+    *have = need;
+    return FFSAT_OK;
+}
+
+int ffsat_step_pgfp(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat_pgfp_args *args,
+                    uint8_t *solved, int32_t *n_unsat, void *stream) {
+    t_err.clear();
+    t_launches = 0;
+    if (!I || !args) return fail(FFSAT_ERR_ARG, "NULL argument");
+    if (B < 0 || args->T < 0) return fail(FFSAT_ERR_ARG, "B and T must be >= 0");
+    if (!(args->eta0 > 0.0) || !std::isfinite(args->eta0)) return fail(FFSAT_ERR_ARG, "eta0 must be positive");
+    if (!(args->beta > 0.0 && args->beta < 1.0)) return fail(FFSAT_ERR_ARG, "beta must lie in (0, 1)");
+    if (args->maxls < 1) return fail(FFSAT_ERR_ARG, "maxls must be >= 1");
+    if (!(args->eta_min >= 0.0) || !(args->slack >= 0.0) || !std::isfinite(args->slack))
+        return fail(FFSAT_ERR_ARG, "eta_min and slack must be >= 0");
+    int rc = check_dtype(dtype);
+    if (rc) return rc;
+    const bool f64 = dtype == FFSAT_F64;
+    const int mode = f64 ? I->smem_mode64 : I->smem_mode32;
+    if (mode == SMEM_NONE)
+        return fail(FFSAT_ERR_ARG, "the line-search step needs x in shared memory (n = %d is too large)", I->n);
+    if (B == 0) return FFSAT_OK;
+    if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
+    CUDA_TRY(cudaSetDevice(I->device));
+    const size_t elem = f64 ? sizeof(double) : sizeof(float);
+    const size_t need = (size_t)B * (size_t)I->n * elem;
+    FusedArgs a{};
+    a.B = B;
+    a.mode = MODE_PGFP;
+    a.x_in = x;
+    a.x_out = x;
+    a.solved = solved;
+    a.n_unsat = n_unsat;
+    a.sp.T = args->T;
+    a.sp.restart = args->restart;
+    a.sp.lr = args->eta0;
+    a.sp.seed = args->seed;
+    a.sp.epoch = args->epoch;
+    a.sp.b_offset = args->b_offset;
+    a.unsat_counts = args->unsat_counts;
+    a.beta = args->beta;
+    a.eta_min = args->eta_min;
+    a.slack = args->slack;
+    a.maxls = args->maxls;
+    a.iters = args->iters;
+    a.eta_out = args->eta_out;
+    if (mode != SMEM_FULL && mode != SMEM_RES) {
+        rc = grow_scratch(&I->d_scratch, &I->scratch_bytes, need);
+        if (rc) return rc;
+        a.g_scratch = I->d_scratch;
+    }
+    rc = grow_scratch(&I->d_yscratch, &I->yscratch_bytes, need);
+    if (rc) return rc;
+    a.y_scratch = I->d_yscratch;
+    const DevView &V = f64 ? I->V64 : I->V32;
+    CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(B),
+                                                          static_cast<cudaStream_t>(stream), false));
+    t_launches = 1;
+    return FFSAT_OK;
+}
+
 int ffsat_check(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, uint8_t *sat, int32_t *n_unsat,
                 void *stream) {
     t_err.clear();
@@ -1684,6 +1753,7 @@ void ffsat_free(ffsat_instance *I) {
     if (I->d_arena) cudaFree(I->d_arena);
     if (I->d_status) cudaFree(I->d_status);
     if (I->d_scratch) cudaFree(I->d_scratch);
+    if (I->d_yscratch) cudaFree(I->d_yscratch);
     delete I;
 }
 

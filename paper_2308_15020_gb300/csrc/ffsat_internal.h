@@ -95,7 +95,7 @@ constexpr int fused_threads(bool f64, int node_r) {
 }
 
 // Mode of the fused kernel.
-enum : int32_t { MODE_EVAL = 0, MODE_STEP = 1 };
+enum : int32_t { MODE_EVAL = 0, MODE_STEP = 1, MODE_PGFP = 2 };
 
 struct FusedArgs {
     int32_t B;
@@ -109,6 +109,16 @@ struct FusedArgs {
     uint8_t *solved;
     int32_t *n_unsat;
     int32_t *unsat_counts;  // step: per-constraint violation counts added by the final check (may be NULL)
+    // MODE_PGFP (line-search step; sp.lr is the initial step size): backtracking
+    // factor, trials per iteration, smallest step, absolute slack of the
+    // sufficient-decrease test, [B, n] scratch for the extrapolated points, and
+    // optional per-point outputs (iterations taken, final step size)
+    double beta, eta_min, slack;
+    int32_t maxls;
+    int32_t pad2;
+    void *y_scratch;
+    int32_t *iters;
+    double *eta_out;
 };
 
 // One instance of a batch launch.

@@ -501,6 +501,70 @@ struct BlockShared {
     int ired[32];
 };
 
+// One evaluation of every warp task at the point xrow: this thread's share of
+// sum_c w FE_c (up to the constants) is returned; with want_g the gradient
+// contributions are added to G.  Starts and ends with a CTA barrier.
+template <typename R, int NR, int NI, bool SF, int XG, typename Acc>
+__device__ __forceinline__ R eval_tasks(const DevView &V, const Src &S, const R *xrow, const Acc &G, bool want_g,
+                                        int &s_ctr) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_ctr = 0;
+    __syncthreads();
+    R facc = R(0);
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&s_ctr, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= V.n_task) break;
+        const int4 task = S.tasks[t];
+        const int kind = task.x & 0xff;
+        if (kind == TASK_CLAUSE) {
+            if (task.z == 128)
+                clause_task<R, XG, 4>(V, S, task, lane, xrow, G, want_g, facc);
+            else if (task.z == 64)
+                clause_task<R, XG, 2>(V, S, task, lane, xrow, G, want_g, facc);
+            else
+                clause_task<R, XG, 1>(V, S, task, lane, xrow, G, want_g, facc);
+        } else if (kind == TASK_PROD) {
+            prod_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
+        } else {
+            // node tasks carry their literals per lane in bits 16..23
+            const int nr = (task.x >> 16) & 0xff;
+            if constexpr (NR >= 16) {
+                if (nr == 12)
+                    node_task<R, 12, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
+                else
+                    node_task<R, 16, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
+            } else if constexpr (NR > 0) {
+                node_task<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
+            }
+        }
+    }
+    __syncthreads();
+    return facc;
+}
+
+// Correctly rounded multiply and add (no contraction), as the FP64 reference computes.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
+template <typename R>
+__device__ __forceinline__ R clip1(R z) {
+    return z < R(-1) ? R(-1) : (z > R(1) ? R(1) : z);
+}
+
+// Sum over the CTA, result in every thread (uses sh.red; contains barriers).
+__device__ __forceinline__ double block_sum_all(double v, BlockShared &sh) {
+    const double t = block_sum(v, sh.red);
+    if (threadIdx.x == 0) sh.red[0] = t;
+    __syncthreads();
+    const double r = sh.red[0];
+    __syncthreads();
+    return r;
+}
+
 // One point b of one instance: stage x, T projected-GD iterations (or one
 // evaluation), exact check and restart.  All threads of the CTA take part.
 template <typename R, int NR, int NI, int SM, int THREADS>
@@ -523,7 +587,8 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
     const int tid = threadIdx.x, lane = tid & 31;
     R *xs = reinterpret_cast<R *>(smem_raw);
     R *gs = xs + npad;
-    const bool step = A.mode == MODE_STEP;
+    const bool pgfp = A.mode == MODE_PGFP;
+    const bool step = A.mode == MODE_STEP || pgfp;
     const R *x_in = static_cast<const R *>(A.x_in);
     R *x_out = static_cast<R *>(A.x_out);
     R *g_out = static_cast<R *>(A.g);
@@ -581,41 +646,66 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
     if (want_g)
         for (int v = tid; v < glen; v += THREADS) G.zero(v);
 
-    const int iters = step ? A.sp.T : 1;
-    for (int it = 0; it < iters; ++it) {
-        if (tid == 0) s_ctr = 0;
-        __syncthreads();
-        R facc = R(0);
-        for (;;) {
-            int t = 0;
-            if (lane == 0) t = atomicAdd(&s_ctr, 1);
-            t = __shfl_sync(kFull, t, 0);
-            if (t >= V.n_task) break;
-            const int4 task = S.tasks[t];
-            const int kind = task.x & 0xff;
-            if (kind == TASK_CLAUSE) {
-                if (task.z == 128)
-                    clause_task<R, XG, 4>(V, S, task, lane, xrow, G, want_g, facc);
-                else if (task.z == 64)
-                    clause_task<R, XG, 2>(V, S, task, lane, xrow, G, want_g, facc);
-                else
-                    clause_task<R, XG, 1>(V, S, task, lane, xrow, G, want_g, facc);
-            } else if (kind == TASK_PROD) {
-                prod_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
-            } else {
-                // node tasks carry their literals per lane in bits 16..23
-                const int nr = (task.x >> 16) & 0xff;
-                if constexpr (NR >= 16) {
-                    if (nr == 12)
-                        node_task<R, 12, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
-                    else
-                        node_task<R, 16, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
-                } else if constexpr (NR > 0) {
-                    node_task<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
-                }
+    if constexpr (XG != SMEM_NONE) {
+        if (pgfp) {
+            // App. A.3, Alg. PGFP with a FISTA line search (Beck-Teboulle backtracking):
+            // xs holds the point being evaluated (y_k or a trial p), the iterate x_k
+            // lives in the output row and y_k in the caller's scratch row.
+            R *xk = x_out + rowoff;
+            R *ys = static_cast<R *>(A.y_scratch) + rowoff;
+            for (int v = tid; v < n; v += THREADS) {
+                ys[v] = xs[v];
+                xk[v] = xs[v];
             }
+            double eta = A.sp.lr, tk = 1.0;
+            int it = 0;
+            while (it < A.sp.T) {
+                ++it;
+                const double fy = block_sum_all((double)eval_tasks<R, NR, NI, SF, XG>(V, S, xs, G, true, s_ctr), sh);
+                for (int ls = 0; ls < A.maxls; ++ls) {
+                    double d = 0.0, q = 0.0;
+                    const R er = R(eta);
+                    for (int v = tid; v < n; v += THREADS) {
+                        const R y = ys[v];
+                        const R gv = R(G.get(v));
+                        const R p = clip1(add_rn(y, -mul_rn(er, gv)));
+                        const R dz = add_rn(p, -y);
+                        xs[v] = p;
+                        d += (double)gv * (double)dz;
+                        q += (double)dz * (double)dz;
+                    }
+                    d = block_sum_all(d, sh);
+                    q = block_sum_all(q, sh);
+                    const double fp =
+                        block_sum_all((double)eval_tasks<R, NR, NI, SF, XG>(V, S, xs, G, false, s_ctr), sh);
+                    if (fp <= fy + d + q / (2.0 * eta) + A.slack) break;  // same value in every thread
+                    if (ls + 1 < A.maxls) eta *= A.beta;
+                }
+                const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
+                const R mom = R((tk - 1.0) / tn);
+                tk = tn;
+                for (int v = tid; v < n; v += THREADS) {
+                    const R xn = xs[v];
+                    const R z = clip1(add_rn(xn, mul_rn(mom, add_rn(xn, -xk[v]))));
+                    xk[v] = xn;
+                    ys[v] = z;
+                    xs[v] = z;
+                    G.zero(v);
+                }
+                __syncthreads();
+                if (eta < A.eta_min) break;
+            }
+            for (int v = tid; v < n; v += THREADS) xs[v] = xk[v];
+            if (tid == 0) {
+                if (A.iters) A.iters[b] = it;
+                if (A.eta_out) A.eta_out[b] = eta;
+            }
+            __syncthreads();
         }
-        __syncthreads();
+    }
+    const int iters = pgfp ? 0 : (step ? A.sp.T : 1);
+    for (int it = 0; it < iters; ++it) {
+        R facc = eval_tasks<R, NR, NI, SF, XG>(V, S, xrow, G, want_g, s_ctr);
         if (!step) {
             if (A.f) {
                 const double tot = block_sum((double)facc, s_red);

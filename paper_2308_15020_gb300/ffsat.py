@@ -47,6 +47,7 @@ SYMBOLS = (
     "ffsat_eval_grad_plain64",
     "ffsat_step",
     "ffsat_step_noalloc",
+    "ffsat_step_pgfp",
     "ffsat_check",
     "ffsat_unsat_counts",
     "ffsat_erwa_update",
@@ -87,6 +88,13 @@ class Options(C.Structure):
 class StepArgs(C.Structure):
     _fields_ = [("T", C.c_int32), ("restart", C.c_int32), ("lr", C.c_double), ("seed", C.c_uint64),
                 ("epoch", C.c_uint64), ("b_offset", C.c_uint64), ("unsat_counts", C.c_void_p)]
+
+
+class PgfpArgs(C.Structure):
+    _fields_ = [("T", C.c_int32), ("restart", C.c_int32), ("eta0", C.c_double), ("beta", C.c_double),
+                ("maxls", C.c_int32), ("pad", C.c_int32), ("eta_min", C.c_double), ("slack", C.c_double),
+                ("seed", C.c_uint64), ("epoch", C.c_uint64), ("b_offset", C.c_uint64),
+                ("unsat_counts", C.c_void_p), ("iters", C.c_void_p), ("eta_out", C.c_void_p)]
 
 
 class BatchIO(C.Structure):
@@ -135,6 +143,8 @@ def lib():
         L.ffsat_step.restype = C.c_int
         L.ffsat_step_noalloc.argtypes = [_vp, C.c_int32, _vp, C.c_int32, C.POINTER(StepArgs), _vp, _vp, _vp]
         L.ffsat_step_noalloc.restype = C.c_int
+        L.ffsat_step_pgfp.argtypes = [_vp, C.c_int32, _vp, C.c_int32, C.POINTER(PgfpArgs), _vp, _vp, _vp]
+        L.ffsat_step_pgfp.restype = C.c_int
         L.ffsat_check.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp, _vp]
         L.ffsat_check.restype = C.c_int
         L.ffsat_unsat_counts.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, _vp]
@@ -341,6 +351,29 @@ class Instance:
                      _ptr(self._counts_arg(unsat_counts)))
         _check(lib().ffsat_step_noalloc(self.handle, B, x.data_ptr(), _dtype_code(x), C.byref(a), solved.data_ptr(),
                                         n_unsat.data_ptr(), _stream(stream)))
+        return solved, n_unsat
+
+    def step_pgfp(self, x, T: int, eta0: float, beta: float = 0.5, maxls: int = 15, eta_min: float = 1e-12,
+                  slack: Optional[float] = None, seed: int = 0, epoch: int = 0, b_offset: int = 0,
+                  restart: bool = True, solved=None, n_unsat=None, unsat_counts=None, iters=None, eta_out=None,
+                  stream=None):
+        """One round of projected gradient with FISTA line search (``ffsat_step_pgfp``).
+        slack defaults to 1e-6 (FP32) or 0 (FP64) times the sum of the host weights."""
+        import torch
+
+        _need_cuda_contig(x, "x")
+        B = x.shape[0]
+        if solved is None:
+            solved = torch.empty(B, dtype=torch.uint8, device=x.device)
+        if n_unsat is None:
+            n_unsat = torch.empty(B, dtype=torch.int32, device=x.device)
+        if slack is None:
+            slack = (1e-6 if x.dtype == torch.float32 else 0.0) * float(self._w.sum())
+        a = PgfpArgs(int(T), int(restart), float(eta0), float(beta), int(maxls), 0, float(eta_min), float(slack),
+                     int(seed) & (2**64 - 1), int(epoch), int(b_offset), _ptr(self._counts_arg(unsat_counts)),
+                     _ptr(iters), _ptr(eta_out))
+        _check(lib().ffsat_step_pgfp(self.handle, B, x.data_ptr(), _dtype_code(x), C.byref(a), solved.data_ptr(),
+                                     n_unsat.data_ptr(), _stream(stream)))
         return solved, n_unsat
 
     def check(self, x, sat=None, n_unsat=None, stream=None):

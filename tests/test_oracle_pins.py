@@ -446,3 +446,77 @@ def test_step_is_pgd_then_check_then_restart():
             assert np.array_equal(x2[b], want)
         else:
             assert np.array_equal(x2[b], x1[b])
+
+
+# ---------------------------------------------------------------------------------------------
+# Projected-gradient fixed point with FISTA line search (App. A.3)
+# ---------------------------------------------------------------------------------------------
+
+def _unit_clauses(signs, weights):
+    n = len(signs)
+    return gen.from_lists(n, [(gen.OR, 0, [int(s) * (v + 1)]) for v, s in enumerate(signs)], weights)
+
+
+def test_pgfp_linear_objective_reaches_the_vertex_without_backtracking():
+    """Unit clauses make F = sum_v w_v s_v x_v affine: the sufficient-decrease
+    test holds for every step size (so the step never shrinks) and projected
+    gradient steps end at the minimising vertex x_v = -s_v exactly."""
+    rng = np.random.default_rng(1)
+    signs = rng.choice([-1, 1], size=7)
+    w = rng.uniform(0.5, 2.0, size=7)
+    inst = _unit_clauses(signs, w)
+    x0 = rng.uniform(-0.9, 0.9, size=(3, 7))
+    x, ok, nun, its, eta = O.step_pgfp(inst, x0, T=60, eta0=0.05, restart=False)
+    assert np.array_equal(x, -np.broadcast_to(signs, x.shape).astype(float))
+    assert ok.all() and not nun.any()
+    assert np.all(eta == 0.05) and np.all(its == 60)
+
+
+def test_pgfp_momentum_follows_the_fista_sequence():
+    """One variable, affine F = w x, no clipping over three iterations:
+    x1 = x0 - h, x2 = x1 - h (t1 = 1 gives no momentum), and
+    x3 = x2 + m2 (x2 - x1) - h with m2 = (t2 - 1)/t3, t2 = golden ratio,
+    t3 = (1 + sqrt(1 + 4 t2^2))/2 = 2.19352...  (h = eta w)."""
+    inst = _unit_clauses([1], [1.0])
+    h = 0.01
+    x, _, _, _, _ = O.step_pgfp(inst, np.array([[0.5]]), T=3, eta0=h, restart=False)
+    phi = (1 + 5 ** 0.5) / 2
+    t3 = 2.193527085331054
+    assert abs(x[0, 0] - (0.5 - 3 * h - (phi - 1) / t3 * h)) < 1e-15
+
+
+def test_pgfp_line_search_takes_the_first_acceptable_step():
+    """From a large initial step, one iteration returns eta = eta0 beta^i for the
+    smallest i at which p = clip(x0 - eta g) satisfies
+    F(p) <= F(x0) + <g, p - x0> + |p - x0|^2 / (2 eta); the previous step of the
+    sequence violates it (checked with independent evaluations of F)."""
+    inst = gen.concat([gen.random_ksat(30, 120, 3, 4), gen.random_xor(30, 8, 3, 6, 4)])
+    x0 = gen.uniform_points(5, 30, 8, dtype=np.float64)
+    eta0, beta = 8.0, 0.5
+    x1, _, _, its, eta = O.step_pgfp(inst, x0, T=1, eta0=eta0, beta=beta, maxls=30, restart=False)
+    f0, g0 = O.eval_grad(inst, x0)
+
+    def ok(b, e):
+        p = np.clip(x0[b] - e * g0[b], -1, 1)
+        fp, _ = O.eval_grad(inst, p[None])
+        return fp[0] <= f0[b] + g0[b] @ (p - x0[b]) + (p - x0[b]) @ (p - x0[b]) / (2 * e), p
+
+    shrunk = 0
+    for b in range(5):
+        i = round(np.log(eta[b] / eta0) / np.log(beta))
+        assert abs(eta[b] - eta0 * beta ** i) < 1e-12 * eta0
+        good, p = ok(b, eta[b])
+        assert good and np.array_equal(p, x1[b])
+        if i > 0:
+            shrunk += 1
+            assert not ok(b, eta[b] / beta)[0]
+    assert shrunk >= 1 and np.all(its == 1)
+
+
+def test_pgfp_stops_below_the_minimum_step():
+    inst = gen.random_ksat(20, 80, 3, 2)
+    x0 = gen.uniform_points(2, 20, 3, dtype=np.float64)
+    _, _, _, its, eta = O.step_pgfp(inst, x0, T=50, eta0=1e-13, restart=False)
+    assert np.all(its == 1) and np.all(eta <= 1e-13)
+    with pytest.raises(ValueError):
+        O.step_pgfp(inst, x0, T=5, eta0=0.1, beta=1.5)
