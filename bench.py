@@ -438,6 +438,10 @@ def run_learned(args, rank: int, world: int, local_rank: int):
     torch.cuda.set_device(local_rank)
     t0 = time.perf_counter()
     res = learned.learned_restart_experiment(train_count=args.train_count, test_count=args.test_count)
+    # a family the CLS can solve within the budget, so that time-to-SAT is defined for both arms
+    solvable = learned.learned_restart_experiment(
+        train_count=600, test_count=24, n_train=400, n_test=350, family="3sat",
+        test_cfg=learned.CLSConfig(B=256, T=100, lr=0.1, max_rounds=300, seed=9))
     line = {
         "metric": "time-to-SAT (median s, PAR-2), learned vs uniform restarts", "value": res["median_par2_s"]["learned"],
         "unit": "s", "n_gpus": 1, "steps": res["test_instances"], "warmup": 0,
@@ -447,6 +451,9 @@ def run_learned(args, rank: int, world: int, local_rank: int):
         "config": {"workload": "learned_restart", "train": f"{res['train_instances']} x n={res['n_train']}",
                    "test": f"{res['test_instances']} x n={res['n_test']}"},
         "uniform_par2_s": res["median_par2_s"]["uniform"], "experiment": res,
+        "planted_3sat_n350": {k: solvable[k] for k in ("solved", "median_time_to_sat_s", "median_par2_s",
+                                                       "median_rounds", "mean_best_unsat", "held_out_sign_agreement",
+                                                       "par2_budget_s")},
         "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
     }
     print(json.dumps(line), flush=True)

@@ -72,20 +72,19 @@ def test_proposal_restart_is_exact():
             assert np.array_equal(got[b], want)
 
 
-def test_learned_proposal_ab_small():
-    """Train on near-solutions the CLS finds on small planted 3-SAT instances, then
-    compare uniform and learned restarts on held-out instances (same seeds)."""
-    from paper_2308_15020_gb300 import ffsat, learned
+def test_learned_proposal_reduces_time_to_sat():
+    """What the trained network gains over the method without it: trained on the
+    CLS's own best points of 600 planted 3-SAT instances (n = 400, ratio 4.2),
+    restarts drawn around its proposal solve far more held-out instances (n = 350)
+    within the same budget than uniform restarts from the same seeds, so the
+    median time-to-SAT falls from unsolved (PAR-2) to a few rounds."""
+    from paper_2308_15020_gb300 import learned
 
-    cfg = learned.CLSConfig(B=64, T=200, lr=0.01, max_rounds=8, seed=5, noise=0.7)
-    train_set = learned.planted_3sat_family(32, 250, 100)
-    net = ffsat.MPNN(layers=3, seed=11)
-    hist, losses = learned.self_train(net, train_set, cfg, rounds=2, epochs=6, lr=3e-3)
-    assert losses[-1] < losses[0]
-    held = learned.planted_3sat_family(8, 300, 900)
-    agree = learned.sign_agreement(net, held)
-    res = learned.ab_test(net, held, cfg)
-    summ = res.summary()
-    print("targets mean #unsat per round", hist, "held-out sign agreement", agree, "A/B", summ)
-    assert agree > 0.6, agree
-    assert summ["solved"]["learned"] >= summ["solved"]["uniform"]
+    res = learned.learned_restart_experiment(
+        train_count=600, test_count=24, n_train=400, n_test=350, family="3sat",
+        test_cfg=learned.CLSConfig(B=256, T=100, lr=0.1, max_rounds=300, seed=9))
+    print(res)
+    assert res["held_out_sign_agreement"] > 0.7
+    assert res["solved"]["learned"] >= res["solved"]["uniform"] + 6
+    assert res["median_par2_s"]["learned"] < 0.5 * res["median_par2_s"]["uniform"]
+    assert res["mean_best_unsat"]["learned"] < 0.6 * res["mean_best_unsat"]["uniform"]
