@@ -336,25 +336,26 @@ TTS_SEEDS = 20          # satisfiable seeds of the n=100 workload (decided by DP
 TTS_MAX_ROUNDS = 200    # CLS rounds of T iterations before a run counts as unsolved
 
 
-def oracle_time_to_sat(inst, cfg, seed: int):
+def oracle_time_to_sat(inst, cfg, seed: int, target_unsat: int = 0):
     """The same CLS as the GPU run (FP64 PGD rounds, ERWA weights, rephasing
     policy) composed from the oracle's functions on the host cores."""
     sys.path.insert(0, os.path.join(ROOT, "oracle"))
     import oracle as O
 
     phase = {"O": 0, "F": 1, "R": 2}
+    use_erwa = cfg.heuristics if cfg.erwa is None else (cfg.erwa and cfg.heuristics)
     t0 = time.perf_counter()
     x = O.rephase(np.zeros((cfg.B, inst.n)), 2, None, seed=seed, epoch=0)
     w = np.asarray(inst.weights, dtype=np.float64).copy()
     for r in range(cfg.max_rounds):
-        x, solved, _ = O.step(inst, x, T=cfg.T, lr=cfg.lr, seed=seed, epoch=r + 1, restart=False, weights=w)
-        if solved.any():
+        x, solved, nun = O.step(inst, x, T=cfg.T, lr=cfg.lr, seed=seed, epoch=r + 1, restart=False, weights=w)
+        if nun.min() <= target_unsat:
             return True, time.perf_counter() - t0, r + 1
+        ph = 2
         if cfg.heuristics:
-            w = O.erwa(O.unsat_counts(inst, x), w, cfg.alpha)
+            if use_erwa:
+                w = O.erwa(O.unsat_counts(inst, x), w, cfg.alpha)
             ph = phase[cfg.policy[r % len(cfg.policy)]]
-        else:
-            ph = 2
         x = O.rephase(x, ph, solved, seed=seed, epoch=r + 1)
     return False, time.perf_counter() - t0, cfg.max_rounds
 
@@ -422,6 +423,144 @@ def run_tts_3sat(args, rank: int, world: int, local_rank: int):
         "e2e": {"value": float(np.median(e2e)), "unit": "s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                 "note": "instance load (host preprocessing and upload) plus the solve"},
         "gpu_launches": launches, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_paper_benchmark(args, rank: int, world: int, local_rank: int):
+    """The paper's Benchmark 1 (random cardinality, FP64, 32 restart points) or
+    Benchmark 2 (parity learning with error, 1024 restart points): time until a
+    point satisfies every constraint (Benchmark 1) or violates at most e m of
+    them (Benchmark 2), per size N, with ERWA + (ROF) rephasing."""
+    import torch
+
+    from paper_2308_15020_gb300 import ffsat, learned
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    b1 = args.workload == "bench1_cardinality"
+    sizes = [50, 100, 150, 200, 250] if b1 else [20, 30, 40, 50, 60]
+    per = args.instances
+    cfg = learned.CLSConfig(B=32 if b1 else 1024, T=100, lr=0.1, max_rounds=TTS_MAX_ROUNDS if b1 else 2000, seed=13,
+                            heuristics=True, policy="ROF", dtype="f64" if b1 else "f32")
+    clocks = ClockSampler(visible_device_index(local_rank))
+    clocks.start()
+    table, cpu_rows = {}, {}
+    for N in sizes:
+        runs = []
+        for i in range(per):
+            inst = gen.bench1_cardinality(N, 1000 * N + i) if b1 else gen.parity_learning(N, 1000 * N + i)
+            h = ffsat.Instance(inst)
+            learned.warm(h, inst.n, cfg, None)
+            runs.append(learned.time_to_sat(h, inst.n, cfg, cfg.seed + i, None, target_unsat=inst.target_unsat))
+        budget = max([r.seconds for r in runs if not r.solved] or [0.0])
+        par2 = [r.seconds if r.solved else 2 * max(budget, 1e-9) for r in runs]
+        table[N] = {"solved": sum(r.solved for r in runs), "instances": per, "median_par2_s": float(np.median(par2)),
+                    "median_rounds": float(np.median([r.rounds for r in runs]))}
+        if not args.no_cpu_baseline:
+            inst = gen.bench1_cardinality(N, 1000 * N) if b1 else gen.parity_learning(N, 1000 * N)
+            ocfg = learned.CLSConfig(**{**vars(cfg), "max_rounds": min(cfg.max_rounds, 20)})
+            ok, dt, rounds = oracle_time_to_sat(inst, ocfg, cfg.seed, inst.target_unsat)
+            cpu_rows[N] = {"solved": bool(ok), "seconds": dt, "rounds": rounds, "gpu_rounds": runs[0].rounds,
+                           "gpu_seconds": runs[0].seconds}
+    clk = clocks.stop()
+    top = table[sizes[-1]]
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    line = {
+        "metric": ("Benchmark 1 random cardinality" if b1 else "Benchmark 2 parity learning with error")
+                  + ": time-to-solve (median s, PAR-2) at the largest N",
+        "value": top["median_par2_s"], "unit": "s", "n_gpus": 1, "steps": per * len(sizes), "warmup": 1,
+        "ms_per_step": None, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": cfg.dtype, "data": "synthetic (seeded generator of the paper's recipe)",
+        "config": {"workload": args.workload, "sizes": sizes, "instances_per_size": per, "B": cfg.B, "T": cfg.T,
+                   "lr": cfg.lr, "max_rounds": cfg.max_rounds, "heuristics": "ERWA alpha 0.4 + (ROF)"},
+        "per_size": table, "roofline": None,
+        "cpu_baseline": None if not cpu_rows else {
+            "value": None, "unit": "s", "cores": O.max_threads(), "kind": "oracle",
+            "sample": "the first instance of each size with the same CLS on the host, at most 20 rounds",
+            "per_size": cpu_rows},
+        "e2e": None, "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_maxcut(args, rank: int, world: int, local_rank: int):
+    """The paper's Benchmark 3: weighted Max-Cut on planted-partition graphs as
+    weighted 2-XOR, fixed weights and (RF) rephasing (App. "Implementation
+    Details").  Best cut found within a fixed number of CLS rounds on the GPU,
+    against the same CLS on the host cores (the FP64 oracle) given the same wall
+    time."""
+    import torch
+
+    from paper_2308_15020_gb300 import ffsat, learned
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    shapes = [(16, 16), (16, 32), (32, 16), (32, 32)]
+    rounds = args.rounds
+    # the paper's projected gradient with line search: on these dense graphs a
+    # fixed step of 0.1 overshoots (every vertex has hundreds of weighted edges)
+    cfg = learned.CLSConfig(B=1024, T=50, lr=1.0, max_rounds=rounds, seed=17, heuristics=True, erwa=False,
+                            policy="RF", method="pgfp")
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    clocks = ClockSampler(visible_device_index(local_rank))
+    clocks.start()
+    rows = {}
+    for (l, k) in shapes:
+        inst = gen.planted_maxcut(l, k, 1000 * l + k)
+        total = float(inst.weights.sum())
+        h = ffsat.Instance(inst)
+        learned.warm(h, inst.n, cfg, None)
+        S = learned.CLSSearch(h, inst.n, cfg, cfg.seed)
+        best = {"cost": math.inf}
+        f = torch.empty(cfg.B, dtype=torch.float64, device="cuda")
+
+        def keep(x, solved, nun):
+            z = torch.where(x < 0, -1.0, 1.0).to(x.dtype)
+            h.eval_grad(z, f=f, want_g=False)
+            c = float(((f.min() + total) / 2).item())  # F(sgn x) = -total + 2 cost
+            best["cost"] = min(best["cost"], c)
+
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for r in range(rounds):
+            S.round(r, keep)
+        torch.cuda.synchronize()
+        t_gpu = time.perf_counter() - t0
+        # the same CLS on the host for the same wall time (B = one point per host thread)
+        Bc = O.max_threads()
+        x = O.rephase(np.zeros((Bc, inst.n)), 2, None, seed=cfg.seed, epoch=0)
+        best_c, tc, r = math.inf, time.perf_counter(), 0
+        while time.perf_counter() - tc < t_gpu:
+            x, solved, _, _, _ = O.step_pgfp(inst, x, T=cfg.T, eta0=cfg.lr, seed=cfg.seed, epoch=r + 1,
+                                             restart=False)
+            fz, _ = O.eval_grad(inst, np.where(x < 0, -1.0, 1.0))
+            best_c = min(best_c, float(((fz.min() + total) / 2)))
+            x = O.rephase(x, 2 if r % 2 == 0 else 1, solved, seed=cfg.seed, epoch=r + 1)
+            r += 1
+        rows[f"{l}x{k}"] = {"n": inst.n, "edges": inst.m, "total_weight": total,
+                            "gpu_best_cut": total - best["cost"], "gpu_rounds": rounds, "gpu_seconds": t_gpu,
+                            "cpu_best_cut": total - best_c, "cpu_rounds": r, "cpu_points": Bc}
+    clk = clocks.stop()
+    top = rows["32x32"]
+    line = {
+        "metric": "Benchmark 3 weighted Max-Cut (planted partition): best cut weight in a fixed GPU time",
+        "value": top["gpu_best_cut"], "unit": "cut weight", "n_gpus": 1, "steps": rounds, "warmup": 1,
+        "ms_per_step": 1e3 * top["gpu_seconds"] / rounds, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic planted-partition graphs (edge probability 0.5)",
+        "config": {"workload": "bench3_maxcut", "shapes": shapes, "B": cfg.B, "T": cfg.T, "eta0": cfg.lr,
+                   "method": "PGFP with FISTA line search (beta 0.5, 15 trials)", "rounds": rounds,
+                   "heuristics": "fixed weights + (RF)"},
+        "per_shape": rows, "roofline": None,
+        "cpu_baseline": {"value": top["cpu_best_cut"], "unit": "cut weight", "cores": O.max_threads(),
+                         "kind": "oracle", "sample": "the same CLS on the host cores for the GPU's wall time"},
+        "e2e": None, "gpu_launches": None, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
 
@@ -747,9 +886,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cnf_xor_n2000",
-                    choices=list(WORKLOADS) + ["3sat_n100_tts", "learned_restart"])
+                    choices=list(WORKLOADS) + ["3sat_n100_tts", "learned_restart", "bench1_cardinality",
+                                               "bench2_parity", "bench3_maxcut"])
+    ap.add_argument("--rounds", type=int, default=20, help="bench3_maxcut: CLS rounds on the GPU")
     ap.add_argument("--train-count", type=int, default=2000, help="learned_restart: training instances")
     ap.add_argument("--test-count", type=int, default=100, help="learned_restart: held-out instances")
+    ap.add_argument("--instances", type=int, default=10, help="bench1_cardinality / bench2_parity: instances per size")
     ap.add_argument("--T", type=int, default=0, help="PGD iterations per step (0 = workload default)")
     ap.add_argument("--B", type=int, default=0, help="restart points per GPU (0 = workload default)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -761,7 +903,9 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
-    if args.workload in ("3sat_n100_tts", "learned_restart") and args.impl == "reference":
+    if args.workload in ("3sat_n100_tts", "learned_restart", "bench1_cardinality", "bench2_parity",
+                         "bench3_maxcut") and \
+            args.impl == "reference":
         if rank == 0:
             print(json.dumps({"impl": "reference", "unavailable": "time-to-SAT lines time the oracle's CLS inside "
                               "the GPU run (cpu_baseline); use --workload 3sat_n100 for the oracle's rate"}))
@@ -771,6 +915,10 @@ def main():
         run_tts_3sat(args, rank, world, local_rank)
     elif args.workload == "learned_restart":
         run_learned(args, rank, world, local_rank)
+    elif args.workload in ("bench1_cardinality", "bench2_parity"):
+        run_paper_benchmark(args, rank, world, local_rank)
+    elif args.workload == "bench3_maxcut":
+        run_maxcut(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

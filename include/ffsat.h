@@ -115,6 +115,7 @@ typedef struct ffsat_info {
     int64_t device_bytes;  /* device memory held by the instance */
     int32_t autotuned;     /* 1 if node_r was chosen by timing candidates at load */
     float autotune_us[2];  /* measured eval time of the candidates (node R 16/12, node R 8), microseconds */
+    int32_t n_xor2;        /* XOR constraints of <= 2 literals (thread-per-constraint records, like clauses) */
 } ffsat_info;
 
 /* Fill `opt` with the defaults (stable form, closed forms for OR/XOR,

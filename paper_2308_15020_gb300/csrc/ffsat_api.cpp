@@ -43,7 +43,7 @@ int fail(int code, const char *fmt, ...) {
 constexpr int kMaxLen = FFSAT_MAX_LEN;
 constexpr int kPaperMaxLen = 60;
 
-enum ConsClass : int8_t { CLS_CLAUSE3 = 0, CLS_PRODUCT = 1, CLS_NODE = 2, CLS_CONST = 3 };
+enum ConsClass : int8_t { CLS_CLAUSE3 = 0, CLS_PRODUCT = 1, CLS_NODE = 2, CLS_CONST = 3, CLS_XOR2 = 4 };
 
 // v(s) of a symmetric constraint: -1 if s True literals satisfy it, +1 otherwise.
 inline int truth_value(int type, int param, int s) {
@@ -348,8 +348,8 @@ int clause_groups_per_task(int groups, int other_tasks, int warps) {
     return pick;
 }
 
-void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clause, int node_r, int warps,
-                 TaskSet &ts) {
+void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clause, int n_xor2, int node_r,
+                 int warps, TaskSet &ts) {
     ts.tasks.clear();
     ts.node_r = node_r;
     auto group = [&](int first, int count, int kind, int R) {
@@ -377,10 +377,15 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
     // the clause list is padded to whole groups of 32; a task covers 1..kClausePerLane groups
     // (1, 2 or 4 groups: the kernel has one unrolled body for each; a tail that is not
     // a whole task is split into smaller powers of two)
-    const int k = clause_groups_per_task(n_clause / 32, (int)ts.tasks.size(), warps);
-    int c = 0;
-    for (int kk = k; kk >= 1; kk >>= 1)
-        for (; c + 32 * kk <= n_clause; c += 32 * kk) ts.tasks.push_back(make_int4(TASK_CLAUSE, c, 32 * kk, 0));
+    // records [0, n_clause) are clauses, [n_clause, n_clause + n_xor2) short XORs
+    const int k = clause_groups_per_task((n_clause + n_xor2) / 32, (int)ts.tasks.size(), warps);
+    for (int part = 0; part < 2; ++part) {
+        const int kind = part == 0 ? TASK_CLAUSE : TASK_XOR2;
+        const int end = part == 0 ? n_clause : n_clause + n_xor2;
+        int c = part == 0 ? 0 : n_clause;
+        for (int kk = k; kk >= 1; kk >>= 1)
+            for (; c + 32 * kk <= end; c += 32 * kk) ts.tasks.push_back(make_int4(kind, c, 32 * kk, 0));
+    }
 }
 
 int smem_mode_for(int n, size_t elem, size_t image_bytes, int max_smem, size_t &bytes) {
@@ -466,6 +471,12 @@ void fill_weights(ffsat_instance *I) {
             std::memcpy(&I->clauses[s].w, &wf, 4);
             I->clause_wd[s] = wc;
             I->f_const -= wc;  // the kernel accumulates 2 w prod q; FE = 2 prod q - 1
+            break;
+        }
+        case CLS_XOR2: {  // FE = w prod y: no constant part
+            const float wf = (float)wc;
+            std::memcpy(&I->clauses[s].w, &wf, 4);
+            I->clause_wd[s] = wc;
             break;
         }
         case CLS_PRODUCT:
@@ -879,7 +890,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     P->lits_in.assign(lits, lits + P->nnz);
 
     // ---- classify ----
-    std::vector<int32_t> node_c, prod_c, clause_c, const_c;
+    std::vector<int32_t> node_c, prod_c, clause_c, const_c, xor2_c;
     for (int32_t c = 0; c < n_cons; ++c) {
         const int L = (int)(row_ptr[c + 1] - row_ptr[c]);
         P->len[c] = L;
@@ -892,6 +903,9 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
         } else if (!opt.node_all && t == FFSAT_OR && L <= 3) {
             P->cls[c] = CLS_CLAUSE3;
             clause_c.push_back(c);
+        } else if (!opt.node_all && t == FFSAT_XOR && L <= 2) {
+            P->cls[c] = CLS_XOR2;
+            xor2_c.push_back(c);
         } else if (!opt.node_all && t != FFSAT_ATLEAST && L <= 32 * kProdR) {
             P->cls[c] = CLS_PRODUCT;
             prod_c.push_back(c);
@@ -958,8 +972,29 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     bank_order(P->clauses, clause_ids);
     const size_t n_clause_pad = (clause_ids.size() + 31) / 32 * 32;
     P->clauses.resize(n_clause_pad, make_int4(n_vars, n_vars, n_vars, 0));
-    P->clause_wd.assign(n_clause_pad, 0.0);
-    for (size_t k = 0; k < clause_ids.size(); ++k) P->slot[clause_ids[k]] = (int32_t)k;
+    clause_ids.resize(n_clause_pad, -1);
+    // XOR constraints of <= 2 literals: records {l0, l1, dummy, w} after the
+    // clauses, the dummy negated for even parity (FE = w y0 y1 y2), bank-ordered
+    // and padded like the clauses
+    std::vector<int4> x2(xor2_c.size());
+    std::vector<int32_t> x2_ids = xor2_c;
+    for (size_t k = 0; k < xor2_c.size(); ++k) {
+        const int32_t c = xor2_c[k];
+        int32_t l2[2] = {n_vars, n_vars};
+        for (int64_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) l2[i - row_ptr[c]] = pack_lit(lits[i]);
+        const int32_t dummy = (param[c] & 1) ? n_vars : (int32_t)((uint32_t)n_vars | 0x80000000u);
+        x2[k] = make_int4(l2[0], l2[1], dummy, 0);
+    }
+    bank_order(x2, x2_ids);
+    const size_t n_xor2_pad = (x2_ids.size() + 31) / 32 * 32;
+    x2.resize(n_xor2_pad, make_int4(n_vars, n_vars, n_vars, 0));
+    x2_ids.resize(n_xor2_pad, -1);
+    P->clauses.insert(P->clauses.end(), x2.begin(), x2.end());
+    clause_ids.insert(clause_ids.end(), x2_ids.begin(), x2_ids.end());
+    const size_t n_rec = n_clause_pad + n_xor2_pad;
+    P->clause_wd.assign(n_rec, 0.0);
+    for (size_t k = 0; k < clause_ids.size(); ++k)
+        if (clause_ids[k] >= 0) P->slot[clause_ids[k]] = (int32_t)k;
     for (int32_t c : const_c) P->slot[c] = -1;
     fill_weights(P);
 
@@ -970,6 +1005,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     std::vector<int32_t> closed_ids;
     closed_ids.insert(closed_ids.end(), clause_c.begin(), clause_c.end());
     closed_ids.insert(closed_ids.end(), prod_c.begin(), prod_c.end());
+    closed_ids.insert(closed_ids.end(), xor2_c.begin(), xor2_c.end());
 
     // ---- node R and task lists ----
     int nr32 = 0, nr64 = 0;
@@ -981,8 +1017,8 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     P->nr[0] = nr32;
     P->nr[1] = nr64;
     TaskSet ts32, ts64;
-    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, nr32, fused_threads(false, nr32) / 32, ts32);
-    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, nr64, fused_threads(true, nr64) / 32, ts64);
+    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, nr32, fused_threads(false, nr32) / 32, ts32);
+    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, nr64, fused_threads(true, nr64) / 32, ts64);
     P->tasks[0] = ts32.tasks;
     P->tasks[1] = ts64.tasks;
     build_image(P, 0);
@@ -991,7 +1027,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     const bool tune = opt.autotune && !node_c.empty() && opt.node_r == 0 && max_node_len <= 8 * 32;
     if (tune) {
         TaskSet ts8;
-        build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, 8, fused_threads(false, 8) / 32, ts8);
+        build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, 8, fused_threads(false, 8) / 32, ts8);
         P->n_images = 3;
         P->nr[2] = 8;
         P->tasks[2] = ts8.tasks;
@@ -1040,7 +1076,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     V.n = n_vars;
     V.m = n_cons;
     V.n_seg = (int32_t)seg_len.size();
-    V.n_clause = (int32_t)n_clause_pad;
+    V.n_clause = (int32_t)n_rec;
     V.clause_wd = reinterpret_cast<const double *>(base + P->off_clause_wd);
     V.seg_wd = reinterpret_cast<const double *>(base + P->off_seg_wd);
     V.tab_f = reinterpret_cast<const float4 *>(base + o_tf);
@@ -1084,6 +1120,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     inf.m = n_cons;
     inf.nnz = P->nnz;
     inf.n_clause3 = (int32_t)clause_c.size();
+    inf.n_xor2 = (int32_t)xor2_c.size();
     inf.n_product = (int32_t)prod_c.size();
     inf.n_node = (int32_t)node_c.size();
     inf.n_const = (int32_t)const_c.size();

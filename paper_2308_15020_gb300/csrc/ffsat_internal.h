@@ -22,7 +22,10 @@ constexpr int32_t kPadLit = -1;
 // Warp tasks.  task.x = kind | (G << 8) where G = lanes per constraint segment
 // (power of two, 1..32); task.y = first item; task.z = item count; task.w = node
 // count J of the largest constraint in the task (node path only).
-enum : int32_t { TASK_CLAUSE = 0, TASK_PROD = 1, TASK_NODE = 2 };
+// TASK_XOR2: records of XOR constraints of <= 2 literals in the clause array
+// (two literals and the dummy, in any order, the dummy negated for even parity;
+// FP32 weight bits last), same layout and grouping as TASK_CLAUSE.
+enum : int32_t { TASK_CLAUSE = 0, TASK_PROD = 1, TASK_NODE = 2, TASK_XOR2 = 3 };
 
 // Closed-form product constraints: FE = c0 + c1 prod_i (a + b y_i).
 enum : int32_t { PROD_OR = 0, PROD_XOR_EVEN = 1, PROD_XOR_ODD = 2 };

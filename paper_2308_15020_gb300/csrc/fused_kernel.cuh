@@ -203,7 +203,10 @@ __device__ __forceinline__ void load_lits(const int32_t *p, uint32_t (&lp)[RL]) 
 // ---------------------------------------------------------------------------
 // FE = 2 w q0 q1 q2 - w; the constant -w is folded into f_const on the host,
 // so facc collects 2 w q0 q1 q2 only.
-template <typename R, int XG, int CPL, typename Acc>
+// XOR: the record is a short XOR, FE = w y0 y1 y2 where one of the three is the
+// dummy (+1, or -1 when negated: even parity; the bank ordering may put it in
+// any position, and its scatter is skipped like every dummy's).
+template <typename R, int XG, int CPL, bool XOR, typename Acc>
 __device__ __forceinline__ void clause_task(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
                                             const Acc &acc, bool want_g, R &facc) {
     const int n = V.n;
@@ -216,6 +219,17 @@ __device__ __forceinline__ void clause_task(const DevView &V, const Src &S, int4
         const R y0 = gather<R, XG>(xrow, (uint32_t)cl[k].x, n);
         const R y1 = gather<R, XG>(xrow, (uint32_t)cl[k].y, n);
         const R y2 = gather<R, XG>(xrow, (uint32_t)cl[k].z, n);
+        if constexpr (XOR) {
+            const R wy2 = w * y2;
+            const R y01 = y0 * y1;
+            facc += wy2 * y01;
+            if (want_g) {
+                scatter<R>(acc, (uint32_t)cl[k].x, wy2 * y1, n);
+                scatter<R>(acc, (uint32_t)cl[k].y, wy2 * y0, n);
+                scatter<R>(acc, (uint32_t)cl[k].z, w * y01, n);
+            }
+            continue;
+        }
         const R q0 = R(0.5) + R(0.5) * y0;
         const R q1 = R(0.5) + R(0.5) * y1;
         const R q2 = R(0.5) + R(0.5) * y2;
@@ -520,11 +534,18 @@ __device__ __forceinline__ R eval_tasks(const DevView &V, const Src &S, const R 
         const int kind = task.x & 0xff;
         if (kind == TASK_CLAUSE) {
             if (task.z == 128)
-                clause_task<R, XG, 4>(V, S, task, lane, xrow, G, want_g, facc);
+                clause_task<R, XG, 4, false>(V, S, task, lane, xrow, G, want_g, facc);
             else if (task.z == 64)
-                clause_task<R, XG, 2>(V, S, task, lane, xrow, G, want_g, facc);
+                clause_task<R, XG, 2, false>(V, S, task, lane, xrow, G, want_g, facc);
             else
-                clause_task<R, XG, 1>(V, S, task, lane, xrow, G, want_g, facc);
+                clause_task<R, XG, 1, false>(V, S, task, lane, xrow, G, want_g, facc);
+        } else if (kind == TASK_XOR2) {
+            if (task.z == 128)
+                clause_task<R, XG, 4, true>(V, S, task, lane, xrow, G, want_g, facc);
+            else if (task.z == 64)
+                clause_task<R, XG, 2, true>(V, S, task, lane, xrow, G, want_g, facc);
+            else
+                clause_task<R, XG, 1, true>(V, S, task, lane, xrow, G, want_g, facc);
         } else if (kind == TASK_PROD) {
             prod_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
         } else {

@@ -31,7 +31,7 @@ __global__ void erwa_kernel(const WeightSites W, const int32_t *__restrict__ U, 
         W.cons_wd[c] = w;
         const int s = W.slot[c];
         const int wbits = __float_as_int((float)w);
-        if (W.cls[c] == 0) {
+        if (W.cls[c] == 0 || W.cls[c] == 4) {
             W.clause_wd[s] = w;
             for (int k = 0; k < W.n_images; ++k) W.clauses[k][s].w = wbits;
         } else if (W.cls[c] == 1 || W.cls[c] == 2) {

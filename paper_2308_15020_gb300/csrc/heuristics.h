@@ -13,7 +13,7 @@ struct WeightSites {
     double *clause_wd;  // FP64 weight by clause slot
     double *seg_wd;     // FP64 weight by segment slot
     double *cons_wd;    // FP64 weight by constraint (the master copy)
-    const int8_t *cls;  // 0 clause of <= 3 literals, 1 product, 2 node, 3 constant
+    const int8_t *cls;  // 0 clause of <= 3 literals, 1 product, 2 node, 3 constant, 4 XOR of <= 2 literals
     const int32_t *slot;
     const int32_t *row_ptr;
     const int32_t *param;

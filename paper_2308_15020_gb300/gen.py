@@ -42,6 +42,7 @@ class Instance:
     weights: np.ndarray  # float64 [m]
     name: str = ""
     planted: Optional[np.ndarray] = field(default=None, repr=False)  # int8 [n] in {-1,+1}
+    target_unsat: int = 0  # an assignment counts as a solution with at most this many violated constraints
 
     @property
     def m(self) -> int:
@@ -311,6 +312,62 @@ def bench1_cardinality(N: int, seed: int = 0) -> Instance:
     inst = random_atleast(N, m, l, l, seed, k_rule="half_floor", sign_rule="all_same")
     inst.name = f"bench1_N{N}"
     return inst
+
+
+def parity_learning(N: int, seed: int = 0, e: float = 0.25) -> Instance:
+    """Benchmark 2, parity learning with error: a hidden parity function over a
+    subset S of the N variables (each variable in S with probability 1/2) and
+    m = 2N samples a_j ~ U{0,1}^N (an all-zero sample is redrawn) labelled
+    b_j = |S cap a_j| mod 2, of which floor(e m) chosen at random are flipped.
+    Sample j becomes the XOR over {i : a_j,i = 1} with parity b_j; variable i is
+    True (-1) iff i is in S.  The hidden S violates exactly floor(e m)
+    constraints, so a solution is an assignment with at most that many
+    violations (target_unsat)."""
+    rng = _rng(seed, 5)
+    m = 2 * N
+    hidden = np.where(rng.random(N) < 0.5, -1, 1).astype(np.int8)  # -1: i in S
+    rows = []
+    for _ in range(m):
+        a = rng.random(N) < 0.5
+        while not a.any():
+            a = rng.random(N) < 0.5
+        rows.append(np.flatnonzero(a) + 1)
+    par = np.array([int(np.sum(hidden[r - 1] < 0)) & 1 for r in rows], dtype=np.int32)
+    flips = rng.choice(m, size=int(np.floor(e * m)), replace=False)
+    par[flips] ^= 1
+    row_ptr = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int64)
+    lits = np.concatenate(rows).astype(np.int32)
+    return Instance(N, row_ptr, lits, np.full(m, XOR, np.uint8), par, np.ones(m), f"plwe_N{N}", hidden,
+                    int(np.floor(e * m)))
+
+
+def planted_maxcut(l: int, k: int, seed: int = 0, p_edge: float = 0.5) -> Instance:
+    """Benchmark 3, weighted Max-Cut on a planted-partition graph: l clusters of
+    k vertices, each vertex pair joined with probability p_edge (unstated in the
+    paper; 0.5 gives the paper's "more than 260000 edges" at l = k = 32), weight
+    1 inside a cluster and 2 between clusters.  Edge (u, v) becomes the XOR of
+    u and v with odd parity (satisfied iff the edge is cut), weighted by the edge
+    weight; maximising the cut is minimising the weight of violated XORs."""
+    rng = _rng(seed, 6)
+    n = l * k
+    cl = np.repeat(np.arange(l), k)
+    iu, iv = np.triu_indices(n, 1)
+    keep = rng.random(iu.shape[0]) < p_edge
+    iu, iv = iu[keep], iv[keep]
+    w = np.where(cl[iu] == cl[iv], 1.0, 2.0)
+    m = iu.shape[0]
+    lits = np.empty(2 * m, dtype=np.int32)
+    lits[0::2] = iu + 1
+    lits[1::2] = iv + 1
+    row_ptr = np.arange(0, 2 * m + 1, 2, dtype=np.int64)
+    return Instance(n, row_ptr, lits, np.full(m, XOR, np.uint8), np.ones(m, np.int32), w, f"maxcut_{l}x{k}")
+
+
+def cut_weight(inst: Instance, z: np.ndarray) -> float:
+    """Total weight of the cut edges (XOR satisfied) under a +-1 assignment."""
+    u = np.abs(inst.lits[0::2]) - 1
+    v = np.abs(inst.lits[1::2]) - 1
+    return float(np.sum(inst.weights[z[u] != z[v]]))
 
 
 WORKLOADS = {

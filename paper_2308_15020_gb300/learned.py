@@ -26,15 +26,17 @@ class CLSConfig:
     noise: float = 0.7   # proposal restarts: x = clip(p + noise * u)
     seed: int = 1
     heuristics: bool = True  # ERWA weights + rephasing between rounds (else plain restarts)
+    erwa: Optional[bool] = None  # ERWA on/off separately (None: as heuristics); fixed weights + rephasing for optimisation
     alpha: float = 0.4       # ERWA decay (Prop. "Adaptive weight")
     policy: str = "ROF"      # rephasing policy, repeated: R random, O original, F flipped
     dtype: str = "f32"       # real type of the points: "f32" or "f64"
+    method: str = "fixed"    # "fixed": x <- clip(x - lr g) T times; "pgfp": FISTA line search from eta0 = lr
 
 
 _PHASE = {"O": 0, "F": 1, "R": 2}
 
 
-class _Search:
+class CLSSearch:
     """State of one CLS run on one instance: B points, per-round step, and the
     restart rule between rounds -- uniform restarts, or (cfg.heuristics) the
     ERWA update plus the rephasing policy, where the learned arm draws its random
@@ -45,7 +47,8 @@ class _Search:
 
         self.h, self.cfg, self.seed, self.prop = h, cfg, seed, prop
         self.x = torch.zeros(cfg.B, n, dtype=torch.float64 if cfg.dtype == "f64" else torch.float32, device="cuda")
-        self.U = torch.zeros(h.m, dtype=torch.int32, device="cuda") if cfg.heuristics else None
+        self.use_erwa = cfg.heuristics if cfg.erwa is None else (cfg.erwa and cfg.heuristics)
+        self.U = torch.zeros(h.m, dtype=torch.int32, device="cuda") if self.use_erwa else None
         if prop is None:
             h.rephase(self.x, ffsat.FFSAT_PHASE_RANDOM, seed=seed, epoch=0)
         else:
@@ -58,13 +61,18 @@ class _Search:
         cfg, h, x = self.cfg, self.h, self.x
         if self.U is not None:
             self.U.zero_()
-        solved, nun = h.step(x, T=cfg.T, lr=cfg.lr, seed=self.seed, epoch=r + 1, restart=False,
-                             unsat_counts=self.U)
+        if cfg.method == "pgfp":
+            solved, nun = h.step_pgfp(x, T=cfg.T, eta0=cfg.lr, seed=self.seed, epoch=r + 1, restart=False,
+                                      unsat_counts=self.U)
+        else:
+            solved, nun = h.step(x, T=cfg.T, lr=cfg.lr, seed=self.seed, epoch=r + 1, restart=False,
+                                 unsat_counts=self.U)
         if on_checked is not None:
             on_checked(x, solved, nun)
         phase = ffsat.FFSAT_PHASE_RANDOM
         if cfg.heuristics:
-            h.erwa_update(self.U, cfg.alpha)
+            if self.use_erwa:
+                h.erwa_update(self.U, cfg.alpha)
             phase = _PHASE[cfg.policy[r % len(cfg.policy)]]
         if phase == ffsat.FFSAT_PHASE_RANDOM and self.prop is not None:
             ffsat.restart_from_proposal(h, x, self.prop, cfg.noise, solved=solved, seed=self.seed, epoch=r + 1)
@@ -81,7 +89,7 @@ def best_point(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Option
     if cfg.heuristics:
         h.set_weights(h.host_weights)
     prop = None if net is None else net.forward(h)
-    S = _Search(h, n, cfg, seed, prop)
+    S = CLSSearch(h, n, cfg, seed, prop)
     st = {"best": None, "u": math.inf}
 
     def keep_best(x, solved, nun):
@@ -152,9 +160,11 @@ class SatRun:
     best_unsat: int = -1  # fewest violated constraints of any point seen (0 when solved)
 
 
-def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optional[ffsat.MPNN] = None) -> SatRun:
-    """Wall time until some point's sign vector is a model (Alg. 1), with uniform
-    restarts (net None) or restarts drawn around the network's proposal."""
+def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optional[ffsat.MPNN] = None,
+                target_unsat: int = 0) -> SatRun:
+    """Wall time until some point's sign vector is a model (Alg. 1) -- or violates
+    at most target_unsat constraints -- with uniform restarts (net None) or
+    restarts drawn around the network's proposal."""
     import torch
 
     if cfg.heuristics:
@@ -162,13 +172,13 @@ def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optio
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     prop = None if net is None else net.forward(h)
-    S = _Search(h, n, cfg, seed, prop)
+    S = CLSSearch(h, n, cfg, seed, prop)
     best = None
     for r in range(cfg.max_rounds):
         solved, nun = S.round(r)
         m = nun.min()
         best = m if best is None else torch.minimum(best, m)
-        if bool(solved.any().item()):
+        if bool((m <= target_unsat).item()):
             torch.cuda.synchronize()
             return SatRun(True, time.perf_counter() - t0, r + 1, 0)
     torch.cuda.synchronize()

@@ -51,3 +51,36 @@ def test_points():
     z = gen.corner_points(8, 100, 0)
     assert set(np.unique(np.abs(z))) <= {0.0, 1.0}
     assert np.signbit(z[z == 0]).any()
+
+
+def test_parity_learning_recipe():
+    """Benchmark 2: m = 2N XOR samples; the hidden parity violates exactly floor(e m)."""
+    import oracle as O
+
+    for N, seed in ((20, 0), (40, 3), (60, 7)):
+        inst = gen.parity_learning(N, seed)
+        assert inst.m == 2 * N and inst.target_unsat == N // 2
+        assert np.all(inst.ctype == gen.XOR) and np.all(inst.lengths() >= 1)
+        assert abs(inst.lengths().mean() / N - 0.5) < 0.1
+        _, nun = O.check(inst, inst.planted.astype(np.float64)[None])
+        assert nun[0] == inst.target_unsat
+
+
+def test_planted_maxcut_recipe():
+    """Benchmark 3: 2-XOR per edge, weight 1 inside a cluster and 2 across; the
+    weight of cut edges plus the weight the oracle's checker counts as violated
+    is the total."""
+    import oracle as O
+
+    inst = gen.planted_maxcut(4, 6, 2)
+    n = 24
+    assert inst.n == n and np.all(inst.lengths() == 2) and np.all(inst.param == 1)
+    u = np.abs(inst.lits[0::2]) - 1
+    v = np.abs(inst.lits[1::2]) - 1
+    assert np.all(u < v)
+    same = (u // 6) == (v // 6)
+    assert np.array_equal(inst.weights, np.where(same, 1.0, 2.0))
+    assert 0.3 < inst.m / (n * (n - 1) / 2) < 0.7
+    z = np.where(np.arange(n) % 3 == 0, -1, 1)
+    U = O.unsat_counts(inst, z.astype(np.float64)[None])
+    assert gen.cut_weight(inst, z) + float(np.sum(inst.weights[U > 0])) == float(inst.weights.sum())
