@@ -565,6 +565,73 @@ def run_maxcut(args, rank: int, world: int, local_rank: int):
     print(json.dumps(line), flush=True)
 
 
+PAPER_RQ1_SPEEDUP = {"xor1": 1.2, "card1": 1.2, "xor3": 31.36, "card3": 148.59}  # A100 vs 2x EPYC 7773X
+
+
+def run_rq1(args, rank: int, world: int, local_rank: int):
+    """The paper's RQ1 (App. D): time of one evaluation of F and grad F at 10 000
+    random points of each random XOR / cardinality formula, on the GPU (FP32
+    fused, FP64 fused, plain FP64) and by the FP64 oracle on the host cores."""
+    import torch
+
+    from paper_2308_15020_gb300 import ffsat
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    B = 10000
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    rows = {}
+    clocks = ClockSampler(visible_device_index(local_rank))
+    clocks.start()
+    for name in gen.RQ1_SHAPES:
+        inst = gen.rq1(name, 0)
+        h = ffsat.Instance(inst)
+        xn = gen.uniform_points(B, inst.n, 7)
+        x32 = torch.from_numpy(xn).cuda()
+        x64 = x32.double()
+        f = torch.empty(B, dtype=torch.float64, device="cuda")
+        g32, g64 = torch.empty_like(x32), torch.empty_like(x64)
+        ms32 = time_evals(lambda: h.eval_grad(x32, f, g32, stream=stream), flush, 10, stream)
+        ms64 = time_evals(lambda: h.eval_grad(x64, f, g64, stream=stream), flush, 5, stream)
+        msp = time_evals(lambda: h.eval_grad_plain64(x64, f, g64, stream=stream), flush, 3, stream)
+        h.sync_status()
+        # the oracle on a sample of the points, scaled to all B
+        nb = min(B, 4 * O.max_threads())
+        t0 = time.perf_counter()
+        reps = 0
+        while reps == 0 or time.perf_counter() - t0 < args.ref_seconds / len(gen.RQ1_SHAPES):
+            O.eval_grad(inst, xn[:nb].astype(np.float64))
+            reps += 1
+        ms_cpu = 1e3 * (time.perf_counter() - t0) / reps * (B / nb)
+        rows[name] = {"nnz": inst.nnz, "gpu_f32_ms": ms32, "gpu_f64_ms": ms64, "gpu_plain64_ms": msp,
+                      "oracle_ms": ms_cpu, "speedup_f32_vs_oracle": ms_cpu / ms32,
+                      "speedup_f64_vs_oracle": ms_cpu / ms64, "speedup_f32_vs_plain64": msp / ms32,
+                      "gpu_f32_literal_grads_per_s": B * inst.nnz / (ms32 / 1e3),
+                      "paper_speedup_a100_vs_cpu": PAPER_RQ1_SPEEDUP.get(name)}
+    clk = clocks.stop()
+    line = {
+        "metric": "RQ1 gradient time at 10 000 random points: speedup of the FP32 fused kernel over the FP64 oracle "
+                  "on the host cores (card3)", "value": rows["card3"]["speedup_f32_vs_oracle"], "unit": "x",
+        "n_gpus": 1, "steps": 10, "warmup": 1, "ms_per_step": rows["card3"]["gpu_f32_ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic (App. D recipe, n = 1024)",
+        "config": {"workload": "rq1_gradients", "B": B, "formulas": list(gen.RQ1_SHAPES),
+                   "l2": "flushed before every timed evaluation"},
+        "per_formula": rows, "roofline": None,
+        "cpu_baseline": {"value": rows["card3"]["oracle_ms"], "unit": "ms per evaluation of 10 000 points",
+                         "cores": O.max_threads(), "kind": "oracle",
+                         "sample": f"{min(B, 4 * O.max_threads())} points per formula, scaled to 10 000"},
+        "paper_context": "100+x gradient speedup, A100 SXM4 vs 2x AMD EPYC 7773X (1.2x xor1/card1, 31.36x xor3, "
+                         "148.59x card3)",
+        "e2e": None, "gpu_launches": 3 * 10 * len(rows), "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args, rank: int, world: int, local_rank: int):
     """Configuration 5: the restart-proposal network trained on CLS best points of
     planted CNF-XOR n=2000 instances, A/B time-to-SAT on held-out n=5000 ones."""
@@ -887,7 +954,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cnf_xor_n2000",
                     choices=list(WORKLOADS) + ["3sat_n100_tts", "learned_restart", "bench1_cardinality",
-                                               "bench2_parity", "bench3_maxcut"])
+                                               "bench2_parity", "bench3_maxcut", "rq1_gradients"])
     ap.add_argument("--rounds", type=int, default=20, help="bench3_maxcut: CLS rounds on the GPU")
     ap.add_argument("--train-count", type=int, default=2000, help="learned_restart: training instances")
     ap.add_argument("--test-count", type=int, default=100, help="learned_restart: held-out instances")
@@ -904,7 +971,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.workload in ("3sat_n100_tts", "learned_restart", "bench1_cardinality", "bench2_parity",
-                         "bench3_maxcut") and \
+                         "bench3_maxcut", "rq1_gradients") and \
             args.impl == "reference":
         if rank == 0:
             print(json.dumps({"impl": "reference", "unavailable": "time-to-SAT lines time the oracle's CLS inside "
@@ -919,6 +986,8 @@ def main():
         run_paper_benchmark(args, rank, world, local_rank)
     elif args.workload == "bench3_maxcut":
         run_maxcut(args, rank, world, local_rank)
+    elif args.workload == "rq1_gradients":
+        run_rq1(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

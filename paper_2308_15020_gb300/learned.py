@@ -221,7 +221,10 @@ def warm(h: ffsat.Instance, n: int, cfg: CLSConfig, net: Optional[ffsat.MPNN]):
     import torch
 
     x = torch.zeros(cfg.B, n, dtype=torch.float64 if cfg.dtype == "f64" else torch.float32, device="cuda")
-    h.step(x, T=1, lr=cfg.lr, restart=False)
+    if cfg.method == "pgfp":
+        h.step_pgfp(x, T=1, eta0=cfg.lr, restart=False)
+    else:
+        h.step(x, T=1, lr=cfg.lr, restart=False)
     if net is not None:
         net.forward(h)
     torch.cuda.synchronize()
