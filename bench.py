@@ -922,7 +922,7 @@ def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
     roof = {"bound": "alu", "achieved": flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
             "frac": flops / launch_s / 1e12 / peak,
             "peak_source": f"FP32 FMA lanes x 2 x {sm_max:.0f} MHz (max SM clock, {peak_src} peaks file)",
-            "algorithmic_per_launch": flops, "traffic": None}
+            "algorithmic_per_launch": flops, "traffic": profile_traffic("ffsat_batch", args.workload)}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_batch(insts, B, T, lr, target_s=args.cpu_seconds)
