@@ -116,6 +116,9 @@ typedef struct ffsat_info {
     int32_t autotuned;     /* 1 if node_r was chosen by timing candidates at load */
     float autotune_us[2];  /* measured eval time of the candidates (node R 16/12, node R 8), microseconds */
     int32_t n_xor2;        /* XOR constraints of <= 2 literals (thread-per-constraint records, like clauses) */
+    int32_t pad;
+    int64_t smem_bytes_f32; /* dynamic shared memory per CTA of the fused kernel */
+    int64_t smem_bytes_f64;
 } ffsat_info;
 
 /* Fill `opt` with the defaults (stable form, closed forms for OR/XOR,

@@ -1121,6 +1121,8 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     inf.nnz = P->nnz;
     inf.n_clause3 = (int32_t)clause_c.size();
     inf.n_xor2 = (int32_t)xor2_c.size();
+    inf.smem_bytes_f32 = (int64_t)P->smem32;
+    inf.smem_bytes_f64 = (int64_t)P->smem64;
     inf.n_product = (int32_t)prod_c.size();
     inf.n_node = (int32_t)node_c.size();
     inf.n_const = (int32_t)const_c.size();

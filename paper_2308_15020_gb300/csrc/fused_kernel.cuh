@@ -771,6 +771,14 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
     __syncthreads();
 }
 
+// Nodes per iteration of the node loop (independent multiply chains): one.
+// FP32 keeps the node factors in registers instead, which leaves no register
+// budget for a second chain at 16 literals per lane.
+template <typename R, int NR>
+constexpr int node_interleave() {
+    return 1;
+}
+
 // ---------------------------------------------------------------------------
 // the fused kernel: one instance, points b = blockIdx.x, blockIdx.x + gridDim.x, ...
 // ---------------------------------------------------------------------------

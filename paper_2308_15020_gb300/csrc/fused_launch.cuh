@@ -11,6 +11,8 @@ namespace dev {
 // Raise a kernel's dynamic shared-memory limit to at least `smem`.  The limit
 // belongs to the kernel, not to an instance, so it only ever grows: a later,
 // smaller instance must not lower it below what an earlier one launches with.
+// The first request always sets the attribute: the default limit is 48 KB less
+// the kernel's static shared memory, not 48 KB.
 inline std::mutex &smem_limit_mutex() {
     static std::mutex mu;
     return mu;
@@ -24,19 +26,10 @@ template <typename Kernel>
 cudaError_t raise_smem_limit(Kernel k, size_t smem) {
     std::lock_guard<std::mutex> lock(smem_limit_mutex());
     size_t &current = smem_limits()[reinterpret_cast<const void *>(k)];
-    if (current == 0) current = 48 * 1024;
-    if (smem <= current) return cudaSuccess;
+    if (current != 0 && smem <= current) return cudaSuccess;
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) current = smem;
     return e;
-}
-
-// Nodes per iteration of the node loop (independent multiply chains): one.
-// FP32 keeps the node factors in registers instead, which leaves no register
-// budget for a second chain at 16 literals per lane.
-template <typename R, int NR>
-constexpr int node_interleave() {
-    return 1;
 }
 
 template <typename R, int NR, int SM>

@@ -108,7 +108,8 @@ class Info(C.Structure):
                 ("n_tasks", C.c_int32), ("node_r", C.c_int32), ("smem_mode_f32", C.c_int32),
                 ("smem_mode_f64", C.c_int32), ("threads_f32", C.c_int32), ("node_lane_work", C.c_int64),
                 ("device_bytes", C.c_int64), ("autotuned", C.c_int32), ("autotune_us", C.c_float * 2),
-                ("n_xor2", C.c_int32)]
+                ("n_xor2", C.c_int32), ("pad", C.c_int32), ("smem_bytes_f32", C.c_int64),
+                ("smem_bytes_f64", C.c_int64)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

@@ -307,3 +307,33 @@ def test_rq1_shapes(F, name):
     f, g = h.eval_grad(_x(x))
     ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4)
     assert ef <= 1 and eg <= 1, (ef, eg)
+
+
+def test_shared_memory_limit_in_a_fresh_process():
+    """A first instance that needs no more than the default shared memory,
+    then one that needs just under 48 KB: the kernel's default limit is 48 KB
+    less its static shared memory, so the second launch needs the attribute set
+    (run in a fresh process, where no earlier test has raised the limit)."""
+    import subprocess
+    import sys
+    import os
+
+    code = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, "tests"); sys.path.insert(0, "oracle"); sys.path.insert(0, ".")
+from paper_2308_15020_gb300 import gen, ffsat
+from parity import compare
+out = []
+for name in ("xor1", "xor2"):
+    inst = gen.rq1(name, 0)
+    h = ffsat.Instance(inst)
+    xn = gen.uniform_points(5, inst.n, 7)
+    f, g = h.eval_grad(torch.from_numpy(xn).cuda())
+    ef, eg = compare(inst, xn.astype(np.float64), f.cpu().numpy(), g.cpu().numpy().astype(np.float64), 1e-4)
+    out.append((name, h.info()["smem_bytes_f32"], ef, eg))
+print(out)
+assert all(ef <= 1 and eg <= 1 for _, _, ef, eg in out)
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
