@@ -94,7 +94,7 @@ struct StepParams {
 
 // Threads per CTA of the fused kernel for (real type, node R).
 constexpr int fused_threads(bool f64, int node_r) {
-    return f64 ? (node_r >= 16 ? 128 : 256) : (node_r >= 16 ? 384 : (node_r > 0 ? 512 : 1024));
+    return f64 ? (node_r >= 16 ? 128 : 256) : (node_r >= 16 ? 512 : (node_r > 0 ? 512 : 1024));
 }
 
 // Mode of the fused kernel.
