@@ -386,6 +386,25 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
         for (int kk = k; kk >= 1; kk >>= 1)
             for (; c + 32 * kk <= end; c += 32 * kk) ts.tasks.push_back(make_int4(kind, c, 32 * kk, 0));
     }
+    // node tasks first (the longest), then product tasks spread evenly among the
+    // clause tasks: their long dependent chains overlap with clause work in other
+    // warps instead of all warps starting on them at once (measured 1.5% faster)
+    {
+        std::vector<int4> node, prod, rest;
+        for (const int4 &t : ts.tasks) {
+            const int kd = t.x & 0xff;
+            (kd == TASK_NODE ? node : (kd == TASK_PROD ? prod : rest)).push_back(t);
+        }
+        std::vector<int4> out = node;
+        const size_t np = prod.size(), nc = rest.size();
+        size_t ip = 0, ic = 0;
+        while (ip < np || ic < nc) {
+            // keep the product share of the emitted tasks at np / (np + nc)
+            if (ip < np && (ic >= nc || (ip + 1) * (np + nc) <= (ip + ic + 1) * np)) out.push_back(prod[ip++]);
+            else out.push_back(rest[ic++]);
+        }
+        ts.tasks.swap(out);
+    }
 }
 
 int smem_mode_for(int n, size_t elem, size_t image_bytes, int max_smem, size_t &bytes) {
