@@ -1084,6 +1084,28 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     P->off_slot = A.put(P->slot);
     P->off_umax = A.put(std::vector<int32_t>{0});
     const size_t o_nid = A.put(node_c), o_cid = A.put(closed_ids);
+    // start values of the FP32 fixed-point gradient words (see FixAcc): every
+    // clause-record literal and every node-segment literal on a real variable
+    // adds one raw magic-offset value per evaluation
+    std::vector<int32_t> fix_bias(((size_t)n_vars + 2 + 3) & ~size_t(3), 0);
+    {
+        std::vector<uint32_t> deg((size_t)n_vars, 0);
+        auto count = [&](int32_t lp) {
+            const uint32_t v = (uint32_t)lp & 0x7fffffffu;
+            if (v < (uint32_t)n_vars) deg[v]++;
+        };
+        for (const int4 &r : P->clauses) {
+            count(r.x);
+            count(r.y);
+            count(r.z);
+        }
+        for (int s = 0; s < P->n_node_seg; ++s) {
+            const int4 si = P->seg_info[s];
+            for (int i = 0; i < si.y; ++i) count(P->seg_lits[(size_t)si.x + i]);
+        }
+        for (int32_t v = 0; v < n_vars; ++v) fix_bias[v] = (int32_t)(0u - deg[v] * 0x4B400000u);
+    }
+    const size_t o_bias = A.put(fix_bias);
     P->arena_bytes = A.host.size();
     CUDA_TRY(cudaMalloc(&P->d_arena, P->arena_bytes));
     CUDA_TRY(cudaMemcpy(P->d_arena, A.host.data(), P->arena_bytes, cudaMemcpyHostToDevice));
@@ -1113,6 +1135,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     V.param = reinterpret_cast<const int32_t *>(base + o_par);
     V.cons_tab = reinterpret_cast<const int32_t *>(base + o_ctab);
     V.cons_wd = reinterpret_cast<const double *>(base + P->off_cons_wd);
+    V.fix_bias = reinterpret_cast<const int32_t *>(base + o_bias);
     V.status = P->d_status;
     P->V32 = view_for_image(P, V, 0);
     P->V64 = view_for_image(P, V, 1);

@@ -74,6 +74,9 @@ struct DevView {
     // Two-word fixed-point gradient accumulator of the FP32 shared-resident mode:
     // g = hi / 2^S1 + lo / 2^(S1+S2); fix_s1 = 2^S1, fix_s2 = 2^S2 and the inverses.
     float fix_s1, fix_s2, fix_i1, fix_i12;
+    // start value of both fixed-point words of variable v (npad entries):
+    // -(fixed-point contributions v receives per evaluation) * 0x4B400000 mod 2^32
+    const int32_t *fix_bias;
     // exact-check CSR over all constraints (packed literals)
     const int32_t *row_ptr;
     const int32_t *lits;

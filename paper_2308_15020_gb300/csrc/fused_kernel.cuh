@@ -143,19 +143,25 @@ struct PlainAcc {
 // Clause and node contributions (bounded by their weight) go to the fixed-point
 // words; product contributions (XOR and long clauses, whose gradients are
 // products of many factors and can be far below the fixed-point resolution)
-// go to an FP32 word updated with atomicAdd.
+// go to an FP32 word updated with atomicAdd.  The words are added the raw bits
+// of the rounded values, 0x4B400000 + h (the magic constant's bits plus the
+// integer); every variable receives the same number deg_v of fixed-point
+// contributions in every evaluation, so each word starts the evaluation at
+// bias_v = -deg_v * 0x4B400000 (mod 2^32) and ends it holding the exact sum of
+// the integers (two's-complement sums are exact modulo 2^32).
 struct FixAcc {
     int *hi;
     int *lo;
     float *gf;
+    const int32_t *bias;
     float s1, s2, i1, i12;
     __device__ __forceinline__ void add(uint32_t v, float c) const {
         constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
         const float m1 = __fmaf_rn(c, s1, kMagic);  // c 2^S1 is exact; one rounding to an integer
-        const int h = __float_as_int(m1) - 0x4B400000;
+        const int h = __float_as_int(m1);           // 0x4B400000 + round(c 2^S1)
         const float r = __fmaf_rn(c, s1, __fsub_rn(kMagic, m1));  // exact residual in [-1/2, 1/2]
         const float m2 = __fmaf_rn(r, s2, kMagic);
-        const int l = __float_as_int(m2) - 0x4B400000;
+        const int l = __float_as_int(m2);
         const unsigned a = (unsigned)__cvta_generic_to_shared(hi + v);
         const unsigned b = (unsigned)__cvta_generic_to_shared(lo + v);
         asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(h) : "memory");
@@ -166,8 +172,9 @@ struct FixAcc {
         return __fmaf_rn((float)lo[v], i12, __fmaf_rn((float)hi[v], i1, gf[v]));
     }
     __device__ __forceinline__ void zero(int v) const {
-        hi[v] = 0;
-        lo[v] = 0;
+        const int b = bias[v];
+        hi[v] = b;
+        lo[v] = b;
         gf[v] = 0.0f;
     }
 };
@@ -652,6 +659,7 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
         G.hi = reinterpret_cast<int *>(smem_raw + (size_t)npad * 4);
         G.lo = G.hi + npad;
         G.gf = reinterpret_cast<float *>(G.lo + npad);
+        G.bias = V.fix_bias;
         G.s1 = V.fix_s1;
         G.s2 = V.fix_s2;
         G.i1 = V.fix_i1;
