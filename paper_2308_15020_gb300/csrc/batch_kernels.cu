@@ -7,7 +7,7 @@ namespace {
 template <typename R, int NR>
 cudaError_t batch_one(const BatchInst *insts, const int2 *items, int n_items, int *counter, const StepParams &sp,
                       size_t smem, int grid, cudaStream_t s, bool prepare_only, int *blocks_per_sm) {
-    constexpr int TH = fused_threads(sizeof(R) == 8, NR);
+    constexpr int TH = batch_threads_for(sizeof(R) == 8, NR);
     auto k = dev::batch_kernel<R, NR, dev::node_interleave<R, NR>(), TH>;
     if (prepare_only) {
         cudaError_t e = dev::raise_smem_limit(k, smem);
@@ -19,7 +19,7 @@ cudaError_t batch_one(const BatchInst *insts, const int2 *items, int n_items, in
 }
 }  // namespace
 
-int batch_threads(bool f64, int node_r) { return fused_threads(f64, node_r > 0 ? 16 : 0); }
+int batch_threads(bool f64, int node_r) { return batch_threads_for(f64, node_r > 0 ? 16 : 0); }
 
 cudaError_t launch_batch(bool f64, int node_r, const BatchInst *insts, const int2 *items, int n_items, int *counter,
                          const StepParams &sp, size_t smem, int grid, cudaStream_t s, bool prepare_only,

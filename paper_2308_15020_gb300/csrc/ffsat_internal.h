@@ -100,6 +100,12 @@ constexpr int fused_threads(bool f64, int node_r) {
     return f64 ? (node_r >= 16 ? 128 : 256) : (node_r >= 16 ? 512 : (node_r > 0 ? 512 : 1024));
 }
 
+// Threads per CTA of the batch kernel: as the fused kernel, but 384 for the FP32
+// node path (node factors kept in registers, see run_point).
+constexpr int batch_threads_for(bool f64, int node_r) {
+    return (!f64 && node_r >= 16) ? 384 : fused_threads(f64, node_r);
+}
+
 // Mode of the fused kernel.
 enum : int32_t { MODE_EVAL = 0, MODE_STEP = 1, MODE_PGFP = 2 };
 

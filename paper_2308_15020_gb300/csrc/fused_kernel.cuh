@@ -598,10 +598,12 @@ __device__ __forceinline__ double block_sum_all(double v, BlockShared &sh) {
 template <typename R, int NR, int NI, int SM, int THREADS>
 __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, int b, unsigned char *smem_raw,
                                           const Src &S, BlockShared &sh) {
-    // node factors are recomputed in the prefix pass rather than kept in registers:
-    // the registers saved allow 512 instead of 384 threads per CTA (measured 2.6%
-    // faster on the cardinality workload)
-    constexpr bool SF = false;
+    // FP32 node factors: kept in registers between the suffix and the prefix pass,
+    // except for 16 literals per lane at 512 threads per CTA (the single-instance
+    // kernel), which recomputes them to fit the registers (measured 2.6% faster on
+    // the cardinality workload than 384 threads with stored factors; the batch
+    // kernel keeps 384 threads and stored factors, 4% faster on the uneven set)
+    constexpr bool SF = sizeof(R) == 4 && !(NR >= 16 && THREADS > 384);
     // SMEM_RES keeps x and g in shared memory like SMEM_FULL and adds the resident image.
     constexpr bool RES = SM == SMEM_RES;
     constexpr int XG = RES ? SMEM_FULL : SM;
