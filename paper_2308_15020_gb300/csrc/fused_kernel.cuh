@@ -559,8 +559,11 @@ __device__ __forceinline__ R eval_tasks(const DevView &V, const Src &S, const R 
             // node tasks carry their literals per lane in bits 16..23
             const int nr = (task.x >> 16) & 0xff;
             if constexpr (NR >= 16) {
+                // the batch kernel also meets images built with 8 literals per lane
                 if (nr == 12)
                     node_task<R, 12, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
+                else if (nr == 8)
+                    node_task<R, 8, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
                 else
                     node_task<R, 16, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
             } else if constexpr (NR > 0) {

@@ -138,3 +138,22 @@ def test_batch_step_replays_from_a_cuda_graph():
     torch.cuda.synchronize()
     for a, b in zip(got, xs):
         assert torch.allclose(a, b, atol=1e-5)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float64])
+def test_batch_with_eight_literal_node_images(dtype):
+    """Instances whose node path was built with 8 literals per lane (FP64 for
+    constraints of <= 256 literals, or node_r = 8 in FP32) inside a batch whose
+    kernel is the 16-literal one: same results as the single-instance path."""
+    from paper_2308_15020_gb300 import ffsat
+
+    insts = [gen.concat([gen.random_ksat(3000, 9000, 3, 11), gen.random_atleast(3000, 20, 32, 200, 11)]),
+             mixed_instance(22, n=700)]
+    hs = [ffsat.Instance(insts[0], node_r=8), ffsat.Instance(insts[1])]
+    bt = ffsat.Batch(hs)
+    xs = [torch.from_numpy(gen.uniform_points(4, i.n, 60 + k)).to(dtype).cuda() for k, i in enumerate(insts)]
+    fs, gs = bt.eval_grad(xs)
+    tol = 1e-4 if dtype == torch.float32 else 1e-10
+    for k, (inst, h) in enumerate(zip(insts, hs)):
+        ef, eg = compare(inst, xs[k].double().cpu().numpy(), to_np(fs[k]), to_np(gs[k]).astype(np.float64), tol)
+        assert ef <= 1 and eg <= 1, (k, ef, eg)
