@@ -99,3 +99,30 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(ffsat, "LIB_PATH", "/nonexistent/libffsat.so")
     with pytest.raises(FileNotFoundError):
         ffsat.lib()
+
+
+def test_null_instance_is_an_argument_error(F):
+    """Every entry point that takes an instance rejects NULL with FFSAT_ERR_ARG
+    before touching the device."""
+    L = F.lib()
+    a = F.StepArgs(1, 0, 0.1, 0, 0, 0, None)
+    pa = F.PgfpArgs(1, 0, 0.1, 0.5, 4, 0, 1e-12, 0.0, 0, 0, 0, None, None, None)
+    w = np.zeros(4)
+    calls = {
+        "ffsat_set_weights": lambda: L.ffsat_set_weights(None, w.ctypes.data),
+        "ffsat_eval_grad": lambda: L.ffsat_eval_grad(None, 1, None, 0, None, None, None),
+        "ffsat_eval_grad_plain64": lambda: L.ffsat_eval_grad_plain64(None, 1, None, None, None, None),
+        "ffsat_step": lambda: L.ffsat_step(None, 1, None, 0, C.byref(a), None, None, None),
+        "ffsat_step_noalloc": lambda: L.ffsat_step_noalloc(None, 1, None, 0, C.byref(a), None, None, None),
+        "ffsat_step_pgfp": lambda: L.ffsat_step_pgfp(None, 1, None, 0, C.byref(pa), None, None, None),
+        "ffsat_check": lambda: L.ffsat_check(None, 1, None, 0, None, None, None),
+        "ffsat_unsat_counts": lambda: L.ffsat_unsat_counts(None, 1, None, 0, None, None),
+        "ffsat_erwa_update": lambda: L.ffsat_erwa_update(None, None, 0.4, None),
+        "ffsat_rephase": lambda: L.ffsat_rephase(None, 1, None, 0, 1, None, 0, 0, 0, None),
+        "ffsat_get_weights": lambda: L.ffsat_get_weights(None, w.ctypes.data),
+        "ffsat_restart_from_proposal": lambda: L.ffsat_restart_from_proposal(None, 1, None, 0, None, 0.5, None, 0, 0,
+                                                                            0, None),
+    }
+    for name, call in calls.items():
+        assert call() == -1, name
+        assert F.lib().ffsat_last_error().decode(), name
