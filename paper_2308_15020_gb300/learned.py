@@ -49,10 +49,40 @@ class CLSSearch:
         self.x = torch.zeros(cfg.B, n, dtype=torch.float64 if cfg.dtype == "f64" else torch.float32, device="cuda")
         self.use_erwa = cfg.heuristics if cfg.erwa is None else (cfg.erwa and cfg.heuristics)
         self.U = torch.zeros(h.m, dtype=torch.int32, device="cuda") if self.use_erwa else None
+        self.rounds_done = 0
         if prop is None:
             h.rephase(self.x, ffsat.FFSAT_PHASE_RANDOM, seed=seed, epoch=0)
         else:
             ffsat.restart_from_proposal(h, self.x, prop, cfg.noise, seed=seed, epoch=0)
+
+    # -- checkpoint / resume -------------------------------------------------------------
+    def state_dict(self) -> dict:
+        """Everything a later process needs to continue this search exactly: the
+        points, the device weights (ERWA), the rounds done, the seed and the
+        configuration (host copies)."""
+        return {"x": self.x.detach().cpu().clone(), "weights": self.h.get_weights(),
+                "rounds_done": self.rounds_done, "seed": self.seed, "cfg": dict(vars(self.cfg)),
+                "proposal": None if self.prop is None else self.prop.detach().cpu().clone()}
+
+    @classmethod
+    def from_state(cls, h: ffsat.Instance, state: dict) -> "CLSSearch":
+        """Resume a search from state_dict() on a freshly loaded instance.  The
+        next round() should be given r = state["rounds_done"]; the restart draws
+        are keyed by (seed, round), so the continuation matches an uninterrupted
+        run (bit for bit where the gradient accumulation is order-independent:
+        the FP32 shared-memory-resident clause and node paths)."""
+        import torch
+
+        cfg = CLSConfig(**state["cfg"])
+        self = cls.__new__(cls)
+        self.h, self.cfg, self.seed = h, cfg, state["seed"]
+        self.prop = None if state["proposal"] is None else state["proposal"].cuda()
+        self.x = state["x"].cuda()
+        self.use_erwa = cfg.heuristics if cfg.erwa is None else (cfg.erwa and cfg.heuristics)
+        self.U = torch.zeros(h.m, dtype=torch.int32, device="cuda") if self.use_erwa else None
+        self.rounds_done = state["rounds_done"]
+        h.set_weights(state["weights"])
+        return self
 
     def round(self, r: int, on_checked=None):
         """One round: T iterations and the exact check (on_checked(x, solved,
@@ -78,6 +108,7 @@ class CLSSearch:
             ffsat.restart_from_proposal(h, x, self.prop, cfg.noise, solved=solved, seed=self.seed, epoch=r + 1)
         else:
             h.rephase(x, phase, solved=solved, seed=self.seed, epoch=r + 1)
+        self.rounds_done = r + 1
         return solved, nun
 
 
