@@ -443,8 +443,12 @@ def run_paper_benchmark(args, rank: int, world: int, local_rank: int):
     b1 = args.workload == "bench1_cardinality"
     sizes = [50, 100, 150, 200, 250] if b1 else [20, 30, 40, 50, 60]
     per = args.instances
-    cfg = learned.CLSConfig(B=32 if b1 else 1024, T=100, lr=0.1, max_rounds=TTS_MAX_ROUNDS if b1 else 2000, seed=13,
-                            heuristics=True, policy="ROF", dtype="f64" if b1 else "f32")
+    # Benchmark 2 uses the paper's line-search update (PGFP, FISTA backtracking from
+    # eta0 = 1): on these long XORs it solved 4 of 5 N = 50 instances in 300 rounds
+    # where the fixed step of 0.1 solved 1
+    cfg = learned.CLSConfig(B=32 if b1 else 1024, T=100, lr=0.1 if b1 else 1.0,
+                            max_rounds=TTS_MAX_ROUNDS if b1 else 1000, seed=13, heuristics=True, policy="ROF",
+                            dtype="f64" if b1 else "f32", method="fixed" if b1 else "pgfp")
     clocks = ClockSampler(visible_device_index(local_rank))
     clocks.start()
     table, cpu_rows = {}, {}

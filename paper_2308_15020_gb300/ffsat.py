@@ -74,6 +74,29 @@ SYMBOLS = (
 )
 
 
+# NVTX ranges around the library calls (for nsys / ncu timelines), enabled by
+# FFSAT_NVTX=1 in the environment; off by default (no cost beyond one test).
+_NVTX = os.environ.get("FFSAT_NVTX", "0") not in ("", "0")
+
+
+def _traced(fn):
+    if not _NVTX:
+        return fn
+    import functools
+
+    @functools.wraps(fn)
+    def wrapper(*a, **k):
+        import torch
+
+        torch.cuda.nvtx.range_push(f"ffsat.{fn.__qualname__}")
+        try:
+            return fn(*a, **k)
+        finally:
+            torch.cuda.nvtx.range_pop()
+
+    return wrapper
+
+
 class FFSatError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"{ERRORS.get(code, code)}: {msg}")
@@ -276,6 +299,7 @@ class Instance:
         _check(lib().ffsat_instance_info(self.handle, C.byref(inf)))
         return inf.as_dict()
 
+    @_traced
     def set_weights(self, w):
         import numpy as np
 
@@ -291,6 +315,7 @@ class Instance:
         return self._w
 
     # -- hot path ----------------------------------------------------------------------------
+    @_traced
     def eval_grad(self, x, f=None, g=None, want_f: bool = True, want_g: bool = True, stream=None):
         """f[b] = F(x_b) (float64) and g = grad F (dtype of x)."""
         import torch
@@ -306,6 +331,7 @@ class Instance:
         _check(rc)
         return f, g
 
+    @_traced
     def eval_grad_plain64(self, x, f=None, g=None, stream=None):
         import torch
 
@@ -319,6 +345,7 @@ class Instance:
                                              _stream(stream)))
         return f, g
 
+    @_traced
     def step(self, x, T: int, lr: float, seed: int = 0, epoch: int = 0, b_offset: int = 0, restart: bool = True,
              solved=None, n_unsat=None, unsat_counts=None, stream=None):
         """One round of fixed-step projected GD + exact check + restart, in place on x.
@@ -338,6 +365,7 @@ class Instance:
                                 n_unsat.data_ptr(), _stream(stream)))
         return solved, n_unsat
 
+    @_traced
     def step_noalloc(self, x, T: int, lr: float, seed: int = 0, epoch: int = 0, b_offset: int = 0,
                      restart: bool = True, solved=None, n_unsat=None, unsat_counts=None, stream=None):
         """``step`` through ``ffsat_step_noalloc``: no device allocation, static scratch."""
@@ -355,6 +383,7 @@ class Instance:
                                         n_unsat.data_ptr(), _stream(stream)))
         return solved, n_unsat
 
+    @_traced
     def step_pgfp(self, x, T: int, eta0: float, beta: float = 0.5, maxls: int = 15, eta_min: float = 1e-12,
                   slack: Optional[float] = None, seed: int = 0, epoch: int = 0, b_offset: int = 0,
                   restart: bool = True, solved=None, n_unsat=None, unsat_counts=None, iters=None, eta_out=None,
@@ -378,6 +407,7 @@ class Instance:
                                      n_unsat.data_ptr(), _stream(stream)))
         return solved, n_unsat
 
+    @_traced
     def check(self, x, sat=None, n_unsat=None, stream=None):
         import torch
 
@@ -403,6 +433,7 @@ class Instance:
             raise ValueError("unsat_counts must be an int32 tensor of m elements")
         return U
 
+    @_traced
     def unsat_counts(self, x, U=None, stream=None):
         """U[c] = number of points of x whose sign vector violates constraint c."""
         import torch
@@ -413,10 +444,12 @@ class Instance:
                                         _stream(stream)))
         return U
 
+    @_traced
     def erwa_update(self, U, alpha: float = 0.4, stream=None):
         """Device ERWA update w <- (1 - alpha) w + alpha U / max U of every weight."""
         _check(lib().ffsat_erwa_update(self.handle, _ptr(self._counts_arg(U)), float(alpha), _stream(stream)))
 
+    @_traced
     def rephase(self, x, phase: int, solved=None, seed: int = 0, epoch: int = 0, b_offset: int = 0, stream=None):
         """Original (0) / flipped (1) / random (2) phase for the unsolved points of x, in place."""
         _need_cuda_contig(x, "x")
@@ -471,6 +504,7 @@ class Batch:
             io[k].b_offset = int(b_offsets[k]) if b_offsets is not None else 0
         return io, dt
 
+    @_traced
     def eval_grad(self, xs, fs=None, gs=None, stream=None):
         import torch
 
@@ -482,6 +516,7 @@ class Batch:
         _check(lib().ffsat_batch_eval_grad(self.handle, io, dt, _stream(stream)))
         return fs, gs
 
+    @_traced
     def step(self, xs, T: int, lr: float, seed: int = 0, epoch: int = 0, restart: bool = True, b_offsets=None,
              solved=None, n_unsat=None, stream=None):
         import torch
