@@ -130,7 +130,9 @@ class ClockSampler:
     def __init__(self, device_index: str):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        import tempfile
+
+        self.path = os.path.join(tempfile.gettempdir(), f"ffsat_clocks_{os.getpid()}.csv")
 
     def mark(self):
         """Only samples taken after this call count (the timed region)."""

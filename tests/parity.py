@@ -4,9 +4,9 @@ Tolerance (FP32 path).  Every constraint value FE_c lies in [-1, 1] and the
 stable node form keeps every factor and partial product inside the unit disc,
 so the FP32 rounding error of one constraint is absolute, of order
 L * eps32 * sum_j |d_j| (at most ~1e-5 for L = 512), not relative to the
-possibly tiny value of one term.  We therefore compare against the condition
-scale of each sum, as in the north-star's "1e-4 relative" read for sums of
-signed terms:
+possibly tiny value of one term.  We therefore read the 1e-4 relative
+tolerance of the FP32 path against the condition scale of each sum of signed
+terms:
     |f - f*| <= 1e-4 * max(|f*|, sum_c w_c |FE_c*|)
     |g_v - g*_v| <= 1e-4 * max(|g*_v|, A_v),  A_v = sum_{c ni v} w_c max(|dFE_c/dy_v|, 1e-2 [node path])
 (the node path carries every at-least-K constraint, and clauses and XORs too
