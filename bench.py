@@ -387,7 +387,7 @@ def run_tts_3sat(args, rank: int, world: int, local_rank: int):
         h = ffsat.Instance(inst)
         t_load = time.perf_counter() - t0
         learned.warm(h, inst.n, cfg, None)
-        r = learned.time_to_sat(h, inst.n, cfg, cfg.seed + 7919 * k, None)
+        r = learned.time_to_sat_graph(h, inst.n, cfg, cfg.seed + 7919 * k)
         runs.append(r)
         e2e.append(t_load + r.seconds)
         launches += 5 * r.rounds  # per round: the step, the three ERWA kernels, the rephase
@@ -419,6 +419,8 @@ def run_tts_3sat(args, rank: int, world: int, local_rank: int):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded generator; satisfiability of each seed decided by DPLL)",
         "config": {"workload": "3sat_n100_tts", "n": 100, "m": 426, "B": cfg.B, "pgd_iters_per_round": cfg.T,
+                   "rounds": "each period of the policy (3 rounds) captured in a CUDA graph and replayed; "
+                             "the stop test after each replay",
                    "lr": cfg.lr, "max_rounds": cfg.max_rounds, "heuristics": "ERWA alpha 0.4 + (ROF) rephasing",
                    "seeds": [s_ for s_, _ in chosen], "dpll_selection_s": t_sel},
         "solved": sum(r.solved for r in runs), "median_rounds": float(np.median([r.rounds for r in runs])),
@@ -460,7 +462,7 @@ def run_paper_benchmark(args, rank: int, world: int, local_rank: int):
             inst = gen.bench1_cardinality(N, 1000 * N + i) if b1 else gen.parity_learning(N, 1000 * N + i)
             h = ffsat.Instance(inst)
             learned.warm(h, inst.n, cfg, None)
-            runs.append(learned.time_to_sat(h, inst.n, cfg, cfg.seed + i, None, target_unsat=inst.target_unsat))
+            runs.append(learned.time_to_sat_graph(h, inst.n, cfg, cfg.seed + i, target_unsat=inst.target_unsat))
         budget = max([r.seconds for r in runs if not r.solved] or [0.0])
         par2 = [r.seconds if r.solved else 2 * max(budget, 1e-9) for r in runs]
         table[N] = {"solved": sum(r.solved for r in runs), "instances": per, "median_par2_s": float(np.median(par2)),

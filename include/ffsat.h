@@ -277,6 +277,14 @@ int ffsat_erwa_update(ffsat_instance *inst, const int32_t *U, double alpha, void
 int ffsat_rephase(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, int32_t phase, const uint8_t *solved,
                   uint64_t seed, uint64_t epoch, uint64_t b_offset, void *stream);
 
+/* ffsat_rephase with the epoch read on the device from *epoch_dev (a uint64 in
+ * device memory) when the kernel runs, so that a CUDA graph that captures the
+ * call draws fresh random phases on every replay when something in the graph
+ * advances the counter.  Errors: as ffsat_rephase, and FFSAT_ERR_ARG for a NULL
+ * epoch_dev. */
+int ffsat_rephase_at(ffsat_instance *inst, int32_t B, void *x, int32_t dtype, int32_t phase, const uint8_t *solved,
+                     uint64_t seed, const uint64_t *epoch_dev, uint64_t b_offset, void *stream);
+
 /* Copy the current device weights (after ERWA updates) into a HOST array of
  * n_cons doubles.  Synchronises the device. */
 int ffsat_get_weights(ffsat_instance *inst, double *weights);

@@ -1487,8 +1487,8 @@ int ffsat_erwa_update(ffsat_instance *I, const int32_t *U, double alpha, void *s
     return FFSAT_OK;
 }
 
-int ffsat_rephase(ffsat_instance *I, int32_t B, void *x, int32_t dtype, int32_t phase, const uint8_t *solved,
-                  uint64_t seed, uint64_t epoch, uint64_t b_offset, void *stream) {
+static int rephase_impl(ffsat_instance *I, int32_t B, void *x, int32_t dtype, int32_t phase, const uint8_t *solved,
+                        uint64_t seed, uint64_t epoch, const uint64_t *epoch_dev, uint64_t b_offset, void *stream) {
     t_err.clear();
     t_launches = 0;
     if (!I) return fail(FFSAT_ERR_ARG, "instance is NULL");
@@ -1501,10 +1501,21 @@ int ffsat_rephase(ffsat_instance *I, int32_t B, void *x, int32_t dtype, int32_t 
     if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
     CUDA_TRY(cudaSetDevice(I->device));
     int nl = 0;
-    CUDA_TRY(launch_rephase(dtype == FFSAT_F64, x, B, I->n, phase, solved, seed, epoch, b_offset,
+    CUDA_TRY(launch_rephase(dtype == FFSAT_F64, x, B, I->n, phase, solved, seed, epoch, b_offset, epoch_dev,
                             static_cast<cudaStream_t>(stream), &nl));
     t_launches = nl;
     return FFSAT_OK;
+}
+
+int ffsat_rephase(ffsat_instance *I, int32_t B, void *x, int32_t dtype, int32_t phase, const uint8_t *solved,
+                  uint64_t seed, uint64_t epoch, uint64_t b_offset, void *stream) {
+    return rephase_impl(I, B, x, dtype, phase, solved, seed, epoch, nullptr, b_offset, stream);
+}
+
+int ffsat_rephase_at(ffsat_instance *I, int32_t B, void *x, int32_t dtype, int32_t phase, const uint8_t *solved,
+                     uint64_t seed, const uint64_t *epoch_dev, uint64_t b_offset, void *stream) {
+    if (!epoch_dev) return fail(FFSAT_ERR_ARG, "epoch_dev is NULL");
+    return rephase_impl(I, B, x, dtype, phase, solved, seed, 0, epoch_dev, b_offset, stream);
 }
 
 int ffsat_get_weights(ffsat_instance *I, double *weights) {

@@ -71,9 +71,12 @@ __global__ void __launch_bounds__(512) f_const_kernel(const WeightSites W, doubl
 // NULL): phase 0 keeps x (original), 1 negates it (flipped), 2 draws it
 // uniformly from [-1, 1)^n with the restart generator keyed by (seed, epoch,
 // b_offset + b) (random).
+// With epoch_dev set, the epoch is read from device memory (a counter that a
+// captured CUDA graph advances between replays).
 template <typename R>
 __global__ void rephase_kernel(R *__restrict__ x, int B, int n, int phase, const uint8_t *__restrict__ solved,
-                               uint64_t seed, uint64_t epoch, uint64_t b_offset) {
+                               uint64_t seed, uint64_t epoch, uint64_t b_offset, const uint64_t *epoch_dev) {
+    if (epoch_dev) epoch = *epoch_dev;
     for (int b = blockIdx.x; b < B; b += gridDim.x) {
         if (solved && solved[b]) continue;
         R *xb = x + (size_t)b * (size_t)n;
@@ -105,16 +108,17 @@ cudaError_t launch_erwa(const WeightSites &W, const int32_t *U, int32_t *umax, d
 }
 
 cudaError_t launch_rephase(bool f64, void *x, int B, int n, int phase, const uint8_t *solved, uint64_t seed,
-                           uint64_t epoch, uint64_t b_offset, cudaStream_t s, int *launches) {
+                           uint64_t epoch, uint64_t b_offset, const uint64_t *epoch_dev, cudaStream_t s,
+                           int *launches) {
     if (launches) *launches = 0;
     if (B <= 0 || phase == 0) return cudaSuccess;
     const int grid = std::min(B, 1 << 20);
     if (f64)
         dev::rephase_kernel<double><<<grid, 256, 0, s>>>(static_cast<double *>(x), B, n, phase, solved, seed, epoch,
-                                                         b_offset);
+                                                         b_offset, epoch_dev);
     else
         dev::rephase_kernel<float><<<grid, 256, 0, s>>>(static_cast<float *>(x), B, n, phase, solved, seed, epoch,
-                                                        b_offset);
+                                                        b_offset, epoch_dev);
     if (launches) *launches = 1;
     return cudaGetLastError();
 }

@@ -23,6 +23,7 @@ struct WeightSites {
 cudaError_t launch_erwa(const WeightSites &W, const int32_t *U, int32_t *umax, double alpha, double *f_const,
                         cudaStream_t s, int *launches);
 cudaError_t launch_rephase(bool f64, void *x, int B, int n, int phase, const uint8_t *solved, uint64_t seed,
-                           uint64_t epoch, uint64_t b_offset, cudaStream_t s, int *launches);
+                           uint64_t epoch, uint64_t b_offset, const uint64_t *epoch_dev, cudaStream_t s,
+                           int *launches);
 
 }  // namespace ffsat

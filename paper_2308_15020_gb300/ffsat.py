@@ -52,6 +52,7 @@ SYMBOLS = (
     "ffsat_unsat_counts",
     "ffsat_erwa_update",
     "ffsat_rephase",
+    "ffsat_rephase_at",
     "ffsat_get_weights",
     "ffsat_batch_create",
     "ffsat_batch_eval_grad",
@@ -179,6 +180,9 @@ def lib():
         L.ffsat_rephase.argtypes = [_vp, C.c_int32, _vp, C.c_int32, C.c_int32, _vp, C.c_uint64, C.c_uint64,
                                     C.c_uint64, _vp]
         L.ffsat_rephase.restype = C.c_int
+        L.ffsat_rephase_at.argtypes = [_vp, C.c_int32, _vp, C.c_int32, C.c_int32, _vp, C.c_uint64, _vp,
+                                       C.c_uint64, _vp]
+        L.ffsat_rephase_at.restype = C.c_int
         L.ffsat_get_weights.argtypes = [_vp, _vp]
         L.ffsat_get_weights.restype = C.c_int
         L.ffsat_batch_create.argtypes = [C.POINTER(_vp), C.c_int32, C.POINTER(_vp)]
@@ -450,9 +454,16 @@ class Instance:
         _check(lib().ffsat_erwa_update(self.handle, _ptr(self._counts_arg(U)), float(alpha), _stream(stream)))
 
     @_traced
-    def rephase(self, x, phase: int, solved=None, seed: int = 0, epoch: int = 0, b_offset: int = 0, stream=None):
-        """Original (0) / flipped (1) / random (2) phase for the unsolved points of x, in place."""
+    def rephase(self, x, phase: int, solved=None, seed: int = 0, epoch: int = 0, b_offset: int = 0, stream=None,
+                epoch_dev=None):
+        """Original (0) / flipped (1) / random (2) phase for the unsolved points of x, in place.
+        With epoch_dev (a one-element int64 device tensor) the epoch is read on the device."""
         _need_cuda_contig(x, "x")
+        if epoch_dev is not None:
+            _check(lib().ffsat_rephase_at(self.handle, x.shape[0], x.data_ptr(), _dtype_code(x), int(phase),
+                                          _ptr(solved), int(seed) & (2**64 - 1), epoch_dev.data_ptr(),
+                                          int(b_offset), _stream(stream)))
+            return x
         _check(lib().ffsat_rephase(self.handle, x.shape[0], x.data_ptr(), _dtype_code(x), int(phase), _ptr(solved),
                                    int(seed) & (2**64 - 1), int(epoch), int(b_offset), _stream(stream)))
         return x

@@ -216,6 +216,61 @@ def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optio
     return SatRun(False, time.perf_counter() - t0, cfg.max_rounds, int(best.item()) if best is not None else -1)
 
 
+def time_to_sat_graph(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, target_unsat: int = 0,
+                      keep: Optional[dict] = None) -> SatRun:
+    """time_to_sat with uniform restarts, where one period of the rephasing
+    policy (len(cfg.policy) rounds: step with violation counts, ERWA update,
+    rephase) is captured once in a CUDA graph and replayed; the random phase reads
+    its epoch from a device counter that the graph advances, so every replay
+    draws what the eager loop would.  The stop test runs after each replay, so
+    rounds are counted in whole periods."""
+    import torch
+
+    if cfg.heuristics:
+        h.set_weights(h.host_weights)
+    warm(h, n, cfg, None)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    S = CLSSearch(h, n, cfg, seed)
+    x = S.x
+    if keep is not None:
+        keep["x"] = x  # the points, for callers that continue or inspect the search
+    B = cfg.B
+    solved = torch.zeros(B, dtype=torch.uint8, device="cuda")
+    nun = torch.zeros(B, dtype=torch.int32, device="cuda")
+    best = torch.full((1,), 2**31 - 1, dtype=torch.int32, device="cuda")
+    ctr = torch.ones(1, dtype=torch.int64, device="cuda")  # round r draws with epoch r + 1
+    policy = cfg.policy if cfg.heuristics else "R"
+
+    def period():
+        for ph in policy:
+            if S.U is not None:
+                S.U.zero_()
+            if cfg.method == "pgfp":
+                h.step_pgfp(x, T=cfg.T, eta0=cfg.lr, seed=seed, restart=False, solved=solved, n_unsat=nun,
+                            unsat_counts=S.U)
+            else:
+                h.step(x, T=cfg.T, lr=cfg.lr, seed=seed, restart=False, solved=solved, n_unsat=nun,
+                       unsat_counts=S.U)
+            torch.minimum(best, nun.min().reshape(1), out=best)
+            if S.use_erwa:
+                h.erwa_update(S.U, cfg.alpha)
+            h.rephase(x, _PHASE[ph], solved=solved, seed=seed, epoch_dev=ctr)
+            ctr.add_(1)
+
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        period()
+    periods = max(1, -(-cfg.max_rounds // len(policy)))
+    for p in range(periods):
+        graph.replay()
+        if int(best.item()) <= target_unsat:
+            torch.cuda.synchronize()
+            return SatRun(True, time.perf_counter() - t0, (p + 1) * len(policy), 0)
+    torch.cuda.synchronize()
+    return SatRun(False, time.perf_counter() - t0, periods * len(policy), int(best.item()))
+
+
 @dataclass
 class ABResult:
     uniform: List[SatRun] = field(default_factory=list)
