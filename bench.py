@@ -419,8 +419,7 @@ def run_tts_3sat(args, rank: int, world: int, local_rank: int):
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded generator; satisfiability of each seed decided by DPLL)",
         "config": {"workload": "3sat_n100_tts", "n": 100, "m": 426, "B": cfg.B, "pgd_iters_per_round": cfg.T,
-                   "rounds": "each period of the policy (3 rounds) captured in a CUDA graph and replayed; "
-                             "the stop test after each replay",
+                   "rounds": "each round a CUDA graph replay (one graph per rephasing phase, captured once)",
                    "lr": cfg.lr, "max_rounds": cfg.max_rounds, "heuristics": "ERWA alpha 0.4 + (ROF) rephasing",
                    "seeds": [s_ for s_, _ in chosen], "dpll_selection_s": t_sel},
         "solved": sum(r.solved for r in runs), "median_rounds": float(np.median([r.rounds for r in runs])),

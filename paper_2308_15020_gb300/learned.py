@@ -218,12 +218,11 @@ def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optio
 
 def time_to_sat_graph(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, target_unsat: int = 0,
                       keep: Optional[dict] = None) -> SatRun:
-    """time_to_sat with uniform restarts, where one period of the rephasing
-    policy (len(cfg.policy) rounds: step with violation counts, ERWA update,
-    rephase) is captured once in a CUDA graph and replayed; the random phase reads
-    its epoch from a device counter that the graph advances, so every replay
-    draws what the eager loop would.  The stop test runs after each replay, so
-    rounds are counted in whole periods."""
+    """time_to_sat with uniform restarts, where each round (step with violation
+    counts, ERWA update, rephase) is a CUDA graph replay: one graph per phase of
+    the rephasing policy, captured once; the random phase reads its epoch from a
+    device counter that the graphs advance, so every replay draws what the eager
+    loop would.  The host reads the best #unsat once per round."""
     import torch
 
     if cfg.heuristics:
@@ -242,33 +241,33 @@ def time_to_sat_graph(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, targ
     ctr = torch.ones(1, dtype=torch.int64, device="cuda")  # round r draws with epoch r + 1
     policy = cfg.policy if cfg.heuristics else "R"
 
-    def period():
-        for ph in policy:
-            if S.U is not None:
-                S.U.zero_()
-            if cfg.method == "pgfp":
-                h.step_pgfp(x, T=cfg.T, eta0=cfg.lr, seed=seed, restart=False, solved=solved, n_unsat=nun,
-                            unsat_counts=S.U)
-            else:
-                h.step(x, T=cfg.T, lr=cfg.lr, seed=seed, restart=False, solved=solved, n_unsat=nun,
-                       unsat_counts=S.U)
-            torch.minimum(best, nun.min().reshape(1), out=best)
-            if S.use_erwa:
-                h.erwa_update(S.U, cfg.alpha)
-            h.rephase(x, _PHASE[ph], solved=solved, seed=seed, epoch_dev=ctr)
-            ctr.add_(1)
+    def one_round(ph):
+        if S.U is not None:
+            S.U.zero_()
+        if cfg.method == "pgfp":
+            h.step_pgfp(x, T=cfg.T, eta0=cfg.lr, seed=seed, restart=False, solved=solved, n_unsat=nun,
+                        unsat_counts=S.U)
+        else:
+            h.step(x, T=cfg.T, lr=cfg.lr, seed=seed, restart=False, solved=solved, n_unsat=nun, unsat_counts=S.U)
+        torch.minimum(best, nun.min().reshape(1), out=best)
+        if S.use_erwa:
+            h.erwa_update(S.U, cfg.alpha)
+        h.rephase(x, _PHASE[ph], solved=solved, seed=seed, epoch_dev=ctr)
+        ctr.add_(1)
 
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        period()
-    periods = max(1, -(-cfg.max_rounds // len(policy)))
-    for p in range(periods):
-        graph.replay()
+    graphs = {}
+    for ph in set(policy):
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            one_round(ph)
+        graphs[ph] = g
+    for r in range(cfg.max_rounds):
+        graphs[policy[r % len(policy)]].replay()
         if int(best.item()) <= target_unsat:
             torch.cuda.synchronize()
-            return SatRun(True, time.perf_counter() - t0, (p + 1) * len(policy), 0)
+            return SatRun(True, time.perf_counter() - t0, r + 1, 0)
     torch.cuda.synchronize()
-    return SatRun(False, time.perf_counter() - t0, periods * len(policy), int(best.item()))
+    return SatRun(False, time.perf_counter() - t0, cfg.max_rounds, int(best.item()))
 
 
 @dataclass
