@@ -620,7 +620,7 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
 
     const int n = V.n;
     const int npad = (n + 2 + 3) & ~3;  // n variables + 2 dummies, rounded to 4
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     R *xs = reinterpret_cast<R *>(smem_raw);
     R *gs = xs + npad;
     const bool pgfp = A.mode == MODE_PGFP;
