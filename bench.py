@@ -294,9 +294,21 @@ def fp32_vs_plain64(h, x, B: int, nnz: int, flush, stream):
     one = time_evals(lambda: h.eval_grad_plain64(x64, f, g64, stream=stream), flush, 1, stream)
     ms64 = time_evals(lambda: h.eval_grad_plain64(x64, f, g64, stream=stream), flush, 3 if one < 500 else 1, stream)
     h.sync_status()
+    # the FP32 result against the FP64 one at the same points (the plain FP64
+    # path matches the FP64 oracle to 1e-10 of the condition scale in the tests)
+    f32 = torch.empty(B, dtype=torch.float64, device="cuda")
+    f64 = torch.empty(B, dtype=torch.float64, device="cuda")
+    h.eval_grad(x32, f32, g32, stream=stream)
+    h.eval_grad_plain64(x64, f64, g64, stream=stream)
+    torch.cuda.synchronize()
+    df = (f32 - f64).abs().max().item()
+    dg = (g32.double() - g64).abs().max().item()
     r32, r64 = B * nnz / (ms32 / 1e3), B * nnz / (ms64 / 1e3)
     return {"fp32_fused_eval": r32, "plain_fp64_gpu_eval": r64, "speedup": r32 / r64, "unit": UNIT,
-            "fp32_eval_ms": ms32, "plain_fp64_eval_ms": ms64}
+            "fp32_eval_ms": ms32, "plain_fp64_eval_ms": ms64,
+            "fp32_error_vs_fp64": {"max_abs_f": df, "max_abs_f_over_max_abs_f64": df / max(f64.abs().max().item(), 1e-300),
+                                   "max_abs_g": dg, "max_abs_g_over_max_abs_g64": dg / max(g64.abs().max().item(), 1e-300),
+                                   "points": B}}
 
 
 def run_reference(args, rank: int, world: int):
