@@ -337,3 +337,20 @@ assert all(ef <= 1 and eg <= 1 for _, _, ef, eg in out)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("B", [1, 153])
+def test_ragged_point_counts(F, B):
+    """One point, and one more point than the GB300 has SMs (a second, nearly
+    empty wave): evaluation against the oracle, and a step whose checker agrees."""
+    inst = gen.cnf_xor_2000(7)
+    h = F.Instance(inst)
+    xn = gen.uniform_points(B, inst.n, 13)
+    x = _x(xn)
+    f, g = h.eval_grad(x)
+    pts = np.unique(np.linspace(0, B - 1, min(B, 6)).astype(int))
+    ef, eg = compare(inst, xn.astype(np.float64), to_np(f), to_np(g).astype(np.float64), 1e-4, points=pts)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+    solved, nun = h.step(x, T=3, lr=0.1, seed=2, epoch=1, restart=False)
+    _, nu_oracle = O.check(inst, to_np(x).astype(np.float64)[pts])
+    assert np.array_equal(to_np(nun)[pts], nu_oracle)
