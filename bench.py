@@ -654,6 +654,65 @@ def run_rq1(args, rank: int, world: int, local_rank: int):
     print(json.dumps(line), flush=True)
 
 
+def run_mpnn(args, rank: int, world: int, local_rank: int):
+    """The restart-proposal network's kernels on configuration-5 shaped
+    instances: one inference (forward) and one training step (forward, loss,
+    backward, Adam) per instance size, CUDA-event timed after warm-up."""
+    import torch
+
+    from paper_2308_15020_gb300 import ffsat
+
+    if rank != 0:
+        return
+    torch.cuda.set_device(local_rank)
+    net = ffsat.MPNN(3, 7)
+    stream = torch.cuda.current_stream()
+    rows = {}
+    for n in (2000, 5000):
+        inst = gen.cnf_xor_2000(11, planted=True, n=n)
+        h = ffsat.Instance(inst)
+        t = torch.from_numpy(inst.planted.astype(np.float32)).cuda()
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        x0 = torch.empty(inst.n, dtype=torch.float32, device="cuda")
+
+        def fwd():
+            net.forward(h, x0)
+
+        def train():
+            net.loss_grad(h, t, loss=loss, x0=x0)
+            net.adam_step(1e-4)
+
+        def timed(fn, reps=20):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record(stream)
+            for _ in range(reps):
+                fn()
+            e_.record(stream)
+            torch.cuda.synchronize()
+            return s_.elapsed_time(e_) / reps
+
+        ms_f, ms_t = timed(fwd), timed(train)
+        H = 64
+        dense = 3 * ((inst.n + inst.m) * (2 * H * H + 2 * 2 * H * H)) + 2 * 8 * H * (inst.n + inst.m)
+        gath = 3 * 2 * 2 * inst.nnz * H
+        flops_f = float(dense + gath)
+        rows[f"n{n}"] = {"n": inst.n, "m": inst.m, "nnz": inst.nnz, "forward_ms": ms_f, "train_step_ms": ms_t,
+                         "forward_gflop": flops_f / 1e9, "forward_tflops": flops_f / (ms_f / 1e3) / 1e12,
+                         "train_tflops_approx": 3 * flops_f / (ms_t / 1e3) / 1e12}
+    line = {
+        "metric": "restart-proposal network: forward and training-step time (ms) on configuration-5 shaped instances",
+        "value": rows["n5000"]["forward_ms"], "unit": "ms", "n_gpus": 1, "steps": 20, "warmup": 3,
+        "ms_per_step": rows["n5000"]["train_step_ms"], "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 weights / fp32 accumulate", "data": "synthetic planted CNF-XOR",
+        "config": {"workload": "mpnn", "layers": 3, "hidden": 64}, "per_size": rows, "roofline": None,
+        "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_learned(args, rank: int, world: int, local_rank: int):
     """Configuration 5: the restart-proposal network trained on CLS best points of
     planted CNF-XOR n=2000 instances, A/B time-to-SAT on held-out n=5000 ones."""
@@ -1004,7 +1063,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cnf_xor_n2000",
                     choices=list(WORKLOADS) + ["3sat_n100_tts", "learned_restart", "bench1_cardinality",
-                                               "bench2_parity", "bench3_maxcut", "rq1_gradients"])
+                                               "bench2_parity", "bench3_maxcut", "rq1_gradients", "mpnn"])
     ap.add_argument("--rounds", type=int, default=20, help="bench3_maxcut: CLS rounds on the GPU")
     ap.add_argument("--train-count", type=int, default=2000, help="learned_restart: training instances")
     ap.add_argument("--test-count", type=int, default=100, help="learned_restart: held-out instances")
@@ -1021,7 +1080,7 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.workload in ("3sat_n100_tts", "learned_restart", "bench1_cardinality", "bench2_parity",
-                         "bench3_maxcut", "rq1_gradients") and \
+                         "bench3_maxcut", "rq1_gradients", "mpnn") and \
             args.impl == "reference":
         if rank == 0:
             print(json.dumps({"impl": "reference", "unavailable": "time-to-SAT lines time the oracle's CLS inside "
@@ -1038,6 +1097,8 @@ def main():
         run_maxcut(args, rank, world, local_rank)
     elif args.workload == "rq1_gradients":
         run_rq1(args, rank, world, local_rank)
+    elif args.workload == "mpnn":
+        run_mpnn(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
