@@ -346,7 +346,7 @@ def run_reference(args, rank: int, world: int):
 
 
 # ---------------------------------------------------------------------------------------------
-# time-to-SAT lines (configuration 1: random 3-SAT n=100; configuration 5: learned restarts)
+# time-to-SAT lines (random 3-SAT n=100 with uniform restarts; learned restarts)
 # ---------------------------------------------------------------------------------------------
 
 TTS_SEEDS = 20          # satisfiable seeds of the n=100 workload (decided by DPLL)
@@ -655,8 +655,8 @@ def run_rq1(args, rank: int, world: int, local_rank: int):
 
 
 def run_mpnn(args, rank: int, world: int, local_rank: int):
-    """The restart-proposal network's kernels on configuration-5 shaped
-    instances: one inference (forward) and one training step (forward, loss,
+    """The restart-proposal network's kernels on planted CNF-XOR instances with
+    n = 2000 and n = 5000 (the sizes it is trained and tested on): one inference (forward) and one training step (forward, loss,
     backward, Adam) per instance size, CUDA-event timed after warm-up."""
     import torch
 
@@ -703,7 +703,7 @@ def run_mpnn(args, rank: int, world: int, local_rank: int):
                          "forward_gflop": flops_f / 1e9, "forward_tflops": flops_f / (ms_f / 1e3) / 1e12,
                          "train_tflops_approx": 3 * flops_f / (ms_t / 1e3) / 1e12}
     line = {
-        "metric": "restart-proposal network: forward and training-step time (ms) on configuration-5 shaped instances",
+        "metric": "restart-proposal network: forward and training-step time (ms), planted CNF-XOR n=5000",
         "value": rows["n5000"]["forward_ms"], "unit": "ms", "n_gpus": 1, "steps": 20, "warmup": 3,
         "ms_per_step": rows["n5000"]["train_step_ms"], "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 weights / fp32 accumulate", "data": "synthetic planted CNF-XOR",

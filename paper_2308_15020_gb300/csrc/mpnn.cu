@@ -37,94 +37,188 @@ namespace mp {
 constexpr int H = 64;
 constexpr int FV = 8;  // variable features (padded)
 constexpr int FC = 8;  // constraint features (padded)
+static_assert(H % 4 == 0 && FV % 4 == 0 && FC % 4 == 0, "dense kernels move float4 groups");
 constexpr uint32_t kSign = 0x80000000u;
 constexpr uint32_t kIdx = 0x7fffffffu;
 
 // ---------------------------------------------------------------------------
-// dense layer: Y[r, :] = act(W [X1[r, :]; X2[r, :]] + b), W is N x (K1 + K2), N = H
+// dense layer: Y[r, :] = act(W [X1[r, :]; X2[r, :]] + b), W is N x (K1 + K2), N = H.
+// Register-tiled FP32 SIMT GEMMs: a CTA owns TR rows, each thread a 4 x 4 block of
+// the output; operands are staged in shared memory in 64-column chunks of the
+// concatenated input, W transposed to [k][o] so that lanes read consecutive
+// banks.  K1 and K2 are multiples of 4, K1 + K2 <= 2H.  Every output element
+// sums its terms in the order bias, k = 0 .. K-1 (fwd) and o = 0 .. H-1 (dX).
 // ---------------------------------------------------------------------------
-constexpr int DR = 4;  // rows per CTA
+constexpr int TR = 32;       // rows per CTA tile
+constexpr int KC = 64;       // input columns per shared-memory chunk
+constexpr int XP = KC + 4;   // padded row pitch of the staged inputs (keeps float4 alignment)
+constexpr int FWD_THREADS = (TR / 4) * (H / 4);  // 128
+
+__device__ __forceinline__ float concat_at(const float *__restrict__ X1, int K1, const float *__restrict__ X2, int K2,
+                                           int r, int k) {
+    return k < K1 ? X1[(size_t)r * K1 + k] : X2[(size_t)r * K2 + (k - K1)];
+}
+
 template <bool RELU>
-__global__ void __launch_bounds__(DR * H) dense_fwd(const float *__restrict__ X1, int K1, const float *__restrict__ X2,
-                                                    int K2, const __nv_bfloat16 *__restrict__ W,
-                                                    const float *__restrict__ b, float *__restrict__ Y, int R) {
-    __shared__ float ws[H * 2 * H];
-    __shared__ float xs[DR][2 * H];
+__global__ void __launch_bounds__(FWD_THREADS) dense_fwd(const float *__restrict__ X1, int K1,
+                                                         const float *__restrict__ X2, int K2,
+                                                         const __nv_bfloat16 *__restrict__ W,
+                                                         const float *__restrict__ b, float *__restrict__ Y, int R) {
+    __shared__ __align__(16) float wt[KC][H];  // wt[k][o] = W[o][c0 + k]
+    __shared__ __align__(16) float xs[TR][XP];
     const int K = K1 + K2;
-    for (int i = threadIdx.x; i < H * K; i += DR * H) ws[i] = __bfloat162float(W[i]);
-    const int r0 = blockIdx.x * DR;
-    for (int i = threadIdx.x; i < DR * K; i += DR * H) {
-        const int rr = i / K, k = i % K, r = r0 + rr;
-        float v = 0.f;
-        if (r < R) v = k < K1 ? X1[(size_t)r * K1 + k] : X2[(size_t)r * K2 + (k - K1)];
-        xs[rr][k] = v;
+    const int t = threadIdx.x, tx = t % (H / 4), ty = t / (H / 4);
+    const int r0 = blockIdx.x * TR;
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float bj = b ? b[tx * 4 + j] : 0.f;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[i][j] = bj;
     }
-    __syncthreads();
-    const int rr = threadIdx.x / H, o = threadIdx.x % H, r = r0 + rr;
-    if (r >= R) return;
-    float acc = b ? b[o] : 0.f;
-    const float *w = ws + o * K;
-    for (int k = 0; k < K; ++k) acc = fmaf(w[k], xs[rr][k], acc);
-    Y[(size_t)r * H + o] = RELU ? fmaxf(acc, 0.f) : acc;
+    for (int c0 = 0; c0 < K; c0 += KC) {
+        const int kc = min(KC, K - c0);  // a multiple of 4
+        __syncthreads();
+        for (int i = t; i < H * kc; i += FWD_THREADS) {
+            const int o = i % H, k = i / H;
+            wt[k][o] = __bfloat162float(W[(size_t)o * K + c0 + k]);
+        }
+        for (int i = t; i < TR * kc; i += FWD_THREADS) {
+            const int rr = i / kc, k = i % kc, r = r0 + rr;
+            xs[rr][k] = r < R ? concat_at(X1, K1, X2, K2, r, c0 + k) : 0.f;
+        }
+        __syncthreads();
+        for (int k = 0; k < kc; k += 4) {
+            float4 xv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) xv[i] = *reinterpret_cast<const float4 *>(&xs[ty * 4 + i][k]);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk) {
+                const float4 wv = *reinterpret_cast<const float4 *>(&wt[k + kk][tx * 4]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float xi = kk == 0 ? xv[i].x : kk == 1 ? xv[i].y : kk == 2 ? xv[i].z : xv[i].w;
+                    acc[i][0] = fmaf(wv.x, xi, acc[i][0]);
+                    acc[i][1] = fmaf(wv.y, xi, acc[i][1]);
+                    acc[i][2] = fmaf(wv.z, xi, acc[i][2]);
+                    acc[i][3] = fmaf(wv.w, xi, acc[i][3]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + ty * 4 + i;
+        if (r >= R) break;
+        float4 v = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
+        if (RELU) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
+        *reinterpret_cast<float4 *>(Y + (size_t)r * H + tx * 4) = v;
+    }
 }
 
-// dX = dY W (split into the two input blocks); dY already includes the activation mask.
-__global__ void __launch_bounds__(DR * 2 * H) dense_bwd_x(const float *__restrict__ dY,
-                                                          const __nv_bfloat16 *__restrict__ W, int K1, int K2,
-                                                          float *__restrict__ dX1, float *__restrict__ dX2,
-                                                          int R) {
-    __shared__ float ws[H * 2 * H];
-    __shared__ float ds[DR][H];
-    const int K = K1 + K2;
-    for (int i = threadIdx.x; i < H * K; i += DR * 2 * H) ws[i] = __bfloat162float(W[i]);
-    const int r0 = blockIdx.x * DR;
-    for (int i = threadIdx.x; i < DR * H; i += DR * 2 * H) {
+// dX = dY W, split into the two input blocks; dY already includes the activation
+// mask.  K = K1 + K2 in {4, 8, .., 2H}; the CTA has (K / 4) * (TR / 4) threads.
+__global__ void __launch_bounds__(2 * H / 4 * (TR / 4)) dense_bwd_x(const float *__restrict__ dY,
+                                                                   const __nv_bfloat16 *__restrict__ W, int K1, int K2,
+                                                                   float *__restrict__ dX1, float *__restrict__ dX2,
+                                                                   int R) {
+    __shared__ __align__(16) float ws[H][2 * H];  // ws[o][k] = W[o][k]
+    __shared__ __align__(16) float ds[TR][H + 4];
+    const int K = K1 + K2, K4 = K / 4, nt = K4 * (TR / 4);
+    const int t = threadIdx.x, tx = t % K4, ty = t / K4;
+    const int r0 = blockIdx.x * TR;
+    for (int i = t; i < H * K; i += nt) ws[i / K][i % K] = __bfloat162float(W[i]);
+    for (int i = t; i < TR * H; i += nt) {
         const int rr = i / H, o = i % H, r = r0 + rr;
         ds[rr][o] = r < R ? dY[(size_t)r * H + o] : 0.f;
     }
     __syncthreads();
-    const int rr = threadIdx.x / (2 * H), k = threadIdx.x % (2 * H), r = r0 + rr;
-    if (r >= R || k >= K) return;
-    float acc = 0.f;
-    for (int o = 0; o < H; ++o) acc = fmaf(ds[rr][o], ws[o * K + k], acc);
-    if (k < K1) {
-        if (dX1) dX1[(size_t)r * K1 + k] = acc;
-    } else if (dX2) {
-        dX2[(size_t)r * K2 + (k - K1)] = acc;
+    float acc[4][4] = {};
+    for (int o = 0; o < H; o += 4) {
+        float4 dv[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) dv[i] = *reinterpret_cast<const float4 *>(&ds[ty * 4 + i][o]);
+#pragma unroll
+        for (int oo = 0; oo < 4; ++oo) {
+            const float4 wv = *reinterpret_cast<const float4 *>(&ws[o + oo][tx * 4]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float di = oo == 0 ? dv[i].x : oo == 1 ? dv[i].y : oo == 2 ? dv[i].z : dv[i].w;
+                acc[i][0] = fmaf(di, wv.x, acc[i][0]);
+                acc[i][1] = fmaf(di, wv.y, acc[i][1]);
+                acc[i][2] = fmaf(di, wv.z, acc[i][2]);
+                acc[i][3] = fmaf(di, wv.w, acc[i][3]);
+            }
+        }
+    }
+    const int k = tx * 4;
+    float *dst = k < K1 ? dX1 : dX2;
+    if (!dst) return;
+    const int pitch = k < K1 ? K1 : K2, kk = k < K1 ? k : k - K1;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = r0 + ty * 4 + i;
+        if (r >= R) break;
+        *reinterpret_cast<float4 *>(dst + (size_t)r * pitch + kk) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
     }
 }
 
-// dW += dY^T [X1, X2], db += sum_r dY  (tiles of 32 rows, FP32 atomics per tile)
-constexpr int WR = 32;
-__global__ void __launch_bounds__(256) dense_bwd_w(const float *__restrict__ dY, const float *__restrict__ X1, int K1,
-                                                   const float *__restrict__ X2, int K2, float *__restrict__ dW,
-                                                   float *__restrict__ db, int R) {
-    __shared__ float ds[WR][H];
-    __shared__ float xs[WR][2 * H];
-    const int K = K1 + K2;
-    const int r0 = blockIdx.x * WR;
-    for (int i = threadIdx.x; i < WR * H; i += 256) {
-        const int rr = i / H, o = i % H, r = r0 + rr;
-        ds[rr][o] = r < R ? dY[(size_t)r * H + o] : 0.f;
+// dW += dY^T [X1, X2], db += sum_r dY.  A grid of at most a few CTAs per SM walks
+// the TR-row tiles; each thread keeps the 4 x 4 blocks (o, k) it owns in registers
+// across tiles and adds them to dW with one FP32 atomic per element at the end.
+constexpr int BW_THREADS = 256;
+template <int NB>  // 4 x 4 blocks per thread: 16 * K / 4 <= NB * BW_THREADS
+__global__ void __launch_bounds__(BW_THREADS) dense_bwd_w(const float *__restrict__ dY, const float *__restrict__ X1,
+                                                          int K1, const float *__restrict__ X2, int K2,
+                                                          float *__restrict__ dW, float *__restrict__ db, int R) {
+    __shared__ __align__(16) float ds[TR][H];
+    __shared__ __align__(16) float xs[TR][2 * H];
+    const int K = K1 + K2, K4 = K / 4, nblk = (H / 4) * K4;
+    const int t = threadIdx.x;
+    float acc[NB][4][4] = {};
+    float bacc = 0.f;
+    const int tiles = (R + TR - 1) / TR;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int r0 = tile * TR;
+        __syncthreads();
+        for (int i = t; i < TR * H; i += BW_THREADS) {
+            const int rr = i / H, o = i % H, r = r0 + rr;
+            ds[rr][o] = r < R ? dY[(size_t)r * H + o] : 0.f;
+        }
+        for (int i = t; i < TR * K; i += BW_THREADS) {
+            const int rr = i / K, k = i % K, r = r0 + rr;
+            xs[rr][k] = r < R ? concat_at(X1, K1, X2, K2, r, k) : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < NB; ++q) {
+            const int blk = t + q * BW_THREADS;
+            if (blk >= nblk) break;
+            const int o = (blk / K4) * 4, k = (blk % K4) * 4;
+            for (int rr = 0; rr < TR; ++rr) {
+                const float4 dv = *reinterpret_cast<const float4 *>(&ds[rr][o]);
+                const float4 xv = *reinterpret_cast<const float4 *>(&xs[rr][k]);
+                const float d[4] = {dv.x, dv.y, dv.z, dv.w}, x[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[q][a][c] = fmaf(d[a], x[c], acc[q][a][c]);
+            }
+        }
+        if (db && t < H)
+            for (int rr = 0; rr < TR; ++rr) bacc += ds[rr][t];
     }
-    for (int i = threadIdx.x; i < WR * K; i += 256) {
-        const int rr = i / K, k = i % K, r = r0 + rr;
-        float v = 0.f;
-        if (r < R) v = k < K1 ? X1[(size_t)r * K1 + k] : X2[(size_t)r * K2 + (k - K1)];
-        xs[rr][k] = v;
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+        const int blk = t + q * BW_THREADS;
+        if (blk >= nblk) break;
+        const int o = (blk / K4) * 4, k = (blk % K4) * 4;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) atomicAdd(&dW[(size_t)(o + a) * K + k + c], acc[q][a][c]);
     }
-    __syncthreads();
-    for (int p = threadIdx.x; p < H * K; p += 256) {
-        const int o = p / K, k = p % K;
-        float acc = 0.f;
-        for (int rr = 0; rr < WR; ++rr) acc = fmaf(ds[rr][o], xs[rr][k], acc);
-        atomicAdd(&dW[p], acc);
-    }
-    if (db && threadIdx.x < H) {
-        float acc = 0.f;
-        for (int rr = 0; rr < WR; ++rr) acc += ds[rr][threadIdx.x];
-        atomicAdd(&db[threadIdx.x], acc);
-    }
+    if (db && t < H) atomicAdd(&db[t], bacc);
 }
 
 // out[r, :] = (norm ? 1/cnt_r : 1) * sum_{e in row r} sign_e * scale[src_e] * src[src_e, :]
@@ -324,9 +418,9 @@ void dense(cudaStream_t s, bool relu, const float *X1, int K1, const float *X2, 
            const float *b, float *Y, int R) {
     if (R <= 0) return;
     if (relu)
-        dense_fwd<true><<<blocks_for(R, DR), DR * H, 0, s>>>(X1, K1, X2, K2, W, b, Y, R);
+        dense_fwd<true><<<blocks_for(R, TR), FWD_THREADS, 0, s>>>(X1, K1, X2, K2, W, b, Y, R);
     else
-        dense_fwd<false><<<blocks_for(R, DR), DR * H, 0, s>>>(X1, K1, X2, K2, W, b, Y, R);
+        dense_fwd<false><<<blocks_for(R, TR), FWD_THREADS, 0, s>>>(X1, K1, X2, K2, W, b, Y, R);
 }
 
 void gather(cudaStream_t s, const float *src, const int32_t *ptr, const uint32_t *idx, const float *scale, int R,
@@ -335,15 +429,29 @@ void gather(cudaStream_t s, const float *src, const int32_t *ptr, const uint32_t
     gather_sum<<<blocks_for((size_t)R * 32, 256), 256, 0, s>>>(src, ptr, idx, scale, R, norm, out);
 }
 
+int sm_count() {
+    static int count = 0;
+    if (!count) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            count = 1;
+    }
+    return count;
+}
+
 void dW(cudaStream_t s, const float *dY, const float *X1, int K1, const float *X2, int K2, float *gW, float *gb,
         int R) {
     if (R <= 0) return;
-    dense_bwd_w<<<blocks_for(R, WR), 256, 0, s>>>(dY, X1, K1, X2, K2, gW, gb, R);
+    const unsigned grid = std::min<unsigned>(blocks_for(R, TR), (unsigned)sm_count());
+    if (4 * (K1 + K2) <= BW_THREADS)
+        dense_bwd_w<1><<<grid, BW_THREADS, 0, s>>>(dY, X1, K1, X2, K2, gW, gb, R);
+    else
+        dense_bwd_w<2><<<grid, BW_THREADS, 0, s>>>(dY, X1, K1, X2, K2, gW, gb, R);
 }
 
 void dX(cudaStream_t s, const float *dY, const __nv_bfloat16 *W, int K1, int K2, float *dX1, float *dX2, int R) {
     if (R <= 0) return;
-    dense_bwd_x<<<blocks_for(R, DR), DR * 2 * H, 0, s>>>(dY, W, K1, K2, dX1, dX2, R);
+    dense_bwd_x<<<blocks_for(R, TR), (K1 + K2) / 4 * (TR / 4), 0, s>>>(dY, W, K1, K2, dX1, dX2, R);
 }
 
 void mask(cudaStream_t s, float *d, const float *y, size_t count) {

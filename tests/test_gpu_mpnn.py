@@ -16,10 +16,17 @@ def _small():
                        gen.random_atleast(80, 6, 5, 30, 4)])
 
 
-def test_loss_and_gradient_match_oracle():
+def _medium():
+    # many 32-row tiles with ragged tails on both sides of the graph
+    return gen.concat([gen.random_ksat(709, 2950, 3, 5), gen.random_xor(709, 40, 3, 20, 5, signs=True),
+                       gen.random_atleast(709, 23, 5, 60, 5)])
+
+
+@pytest.mark.parametrize("make", [_small, _medium], ids=["small", "medium"])
+def test_loss_and_gradient_match_oracle(make):
     from paper_2308_15020_gb300 import ffsat
 
-    inst = _small()
+    inst = make()
     h = ffsat.Instance(inst)
     net = ffsat.MPNN(layers=3, seed=1)
     rng = np.random.default_rng(2)
