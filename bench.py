@@ -377,6 +377,18 @@ def oracle_time_to_sat(inst, cfg, seed: int, target_unsat: int = 0):
     return False, time.perf_counter() - t0, cfg.max_rounds
 
 
+def prime_cls_graphs(inst, cfgs):
+    """One untimed single-round graph-captured CLS run per configuration: the
+    process's first graph capture and lazy kernel loads stay out of the timed
+    runs (every timed run still captures its own graphs)."""
+    from paper_2308_15020_gb300 import ffsat, learned
+
+    h = ffsat.Instance(inst)
+    for c in cfgs:
+        if c is not None:
+            learned.time_to_sat_graph(h, inst.n, learned.CLSConfig(**{**vars(c), "max_rounds": 1}), 0)
+
+
 def run_tts_3sat(args, rank: int, world: int, local_rank: int):
     """Median time-to-SAT over satisfiable seeds of the random 3-SAT n=100
     workload: FP64 points, B=32, T=200, lr=0.1, ERWA + (ROF) rephasing."""
@@ -393,6 +405,7 @@ def run_tts_3sat(args, rank: int, world: int, local_rank: int):
     chosen = gen.satisfiable_3sat_100(TTS_SEEDS, 0)
     t_sel = time.perf_counter() - t_sel
     runs, e2e, launches = [], [], 0
+    prime_cls_graphs(chosen[0][1], [cfg])
     clocks = ClockSampler(visible_device_index(local_rank))
     clocks.start()
     for k, (s_, inst) in enumerate(chosen):
@@ -466,20 +479,34 @@ def run_paper_benchmark(args, rank: int, world: int, local_rank: int):
     cfg = learned.CLSConfig(B=32 if b1 else 1024, T=100, lr=0.1 if b1 else 1.0,
                             max_rounds=TTS_MAX_ROUNDS if b1 else 1000, seed=13, heuristics=True, policy="ROF",
                             dtype="f64" if b1 else "f32", method="fixed" if b1 else "pgfp")
+    # Benchmark 1 also runs as this implementation would be used on a GB300: the
+    # FP32 stable node form (accurate to the FP64 oracle within 1e-4, where the
+    # paper's form needed FP64) and 1024 restart points, on the same instances
+    cfg32 = learned.CLSConfig(**{**vars(cfg), "B": 1024, "dtype": "f32"}) if b1 else None
     clocks = ClockSampler(visible_device_index(local_rank))
     clocks.start()
-    table, cpu_rows = {}, {}
+    table, table32, cpu_rows = {}, {}, {}
+    prime_cls_graphs(gen.bench1_cardinality(sizes[0], 0) if b1 else gen.parity_learning(sizes[0], 0), [cfg, cfg32])
+
+    def summary(runs):
+        budget = max([r.seconds for r in runs if not r.solved] or [0.0])
+        par2 = [r.seconds if r.solved else 2 * max(budget, 1e-9) for r in runs]
+        return {"solved": sum(r.solved for r in runs), "instances": len(runs), "median_par2_s": float(np.median(par2)),
+                "median_rounds": float(np.median([r.rounds for r in runs]))}
+
     for N in sizes:
-        runs = []
+        runs, runs32 = [], []
         for i in range(per):
             inst = gen.bench1_cardinality(N, 1000 * N + i) if b1 else gen.parity_learning(N, 1000 * N + i)
             h = ffsat.Instance(inst)
-            learned.warm(h, inst.n, cfg, None)
-            runs.append(learned.time_to_sat_graph(h, inst.n, cfg, cfg.seed + i, target_unsat=inst.target_unsat))
-        budget = max([r.seconds for r in runs if not r.solved] or [0.0])
-        par2 = [r.seconds if r.solved else 2 * max(budget, 1e-9) for r in runs]
-        table[N] = {"solved": sum(r.solved for r in runs), "instances": per, "median_par2_s": float(np.median(par2)),
-                    "median_rounds": float(np.median([r.rounds for r in runs]))}
+            for c, out in ((cfg, runs), (cfg32, runs32)):
+                if c is None:
+                    continue
+                learned.warm(h, inst.n, c, None)
+                out.append(learned.time_to_sat_graph(h, inst.n, c, c.seed + i, target_unsat=inst.target_unsat))
+        table[N] = summary(runs)
+        if runs32:
+            table32[N] = summary(runs32)
         if not args.no_cpu_baseline:
             inst = gen.bench1_cardinality(N, 1000 * N) if b1 else gen.parity_learning(N, 1000 * N)
             ocfg = learned.CLSConfig(**{**vars(cfg), "max_rounds": min(cfg.max_rounds, 20)})
@@ -500,6 +527,8 @@ def run_paper_benchmark(args, rank: int, world: int, local_rank: int):
         "config": {"workload": args.workload, "sizes": sizes, "instances_per_size": per, "B": cfg.B, "T": cfg.T,
                    "lr": cfg.lr, "max_rounds": cfg.max_rounds, "heuristics": "ERWA alpha 0.4 + (ROF)"},
         "per_size": table, "roofline": None,
+        **({"fp32_b1024": {"note": "the same instances and CLS in FP32 with 1024 restart points",
+                           "value": table32[sizes[-1]]["median_par2_s"], "per_size": table32}} if table32 else {}),
         "cpu_baseline": None if not cpu_rows else {
             "value": None, "unit": "s", "cores": O.max_threads(), "kind": "oracle",
             "sample": "the first instance of each size with the same CLS on the host, at most 20 rounds",
