@@ -404,8 +404,11 @@ def run_tts_3sat(args, rank: int, world: int, local_rank: int):
     t_sel = time.perf_counter()
     chosen = gen.satisfiable_3sat_100(TTS_SEEDS, 0)
     t_sel = time.perf_counter() - t_sel
-    runs, e2e, launches = [], [], 0
-    prime_cls_graphs(chosen[0][1], [cfg])
+    # the same seeds as this implementation would run them on a GB300: FP32 stable
+    # form, 1024 restart points per round
+    cfg32 = learned.CLSConfig(**{**vars(cfg), "B": 1024, "dtype": "f32"})
+    runs, runs32, e2e, launches = [], [], [], 0
+    prime_cls_graphs(chosen[0][1], [cfg, cfg32])
     clocks = ClockSampler(visible_device_index(local_rank))
     clocks.start()
     for k, (s_, inst) in enumerate(chosen):
@@ -418,9 +421,12 @@ def run_tts_3sat(args, rank: int, world: int, local_rank: int):
         runs.append(r)
         e2e.append(t_load + r.seconds)
         launches += 5 * r.rounds  # per round: the step, the three ERWA kernels, the rephase
+        runs32.append(learned.time_to_sat_graph(h, inst.n, cfg32, cfg.seed + 7919 * k))
     clk = clocks.stop()
     budget = max([r.seconds for r in runs if not r.solved] or [0.0])
     par2 = [r.seconds if r.solved else 2 * max(budget, 1e-9) for r in runs]
+    budget32 = max([r.seconds for r in runs32 if not r.solved] or [0.0])
+    par2_32 = [r.seconds if r.solved else 2 * max(budget32, 1e-9) for r in runs32]
     cpu = None
     if not args.no_cpu_baseline:
         sys.path.insert(0, os.path.join(ROOT, "oracle"))
@@ -450,6 +456,9 @@ def run_tts_3sat(args, rank: int, world: int, local_rank: int):
                    "lr": cfg.lr, "max_rounds": cfg.max_rounds, "heuristics": "ERWA alpha 0.4 + (ROF) rephasing",
                    "seeds": [s_ for s_, _ in chosen], "dpll_selection_s": t_sel},
         "solved": sum(r.solved for r in runs), "median_rounds": float(np.median([r.rounds for r in runs])),
+        "fp32_b1024": {"note": "the same seeds and CLS in FP32 with 1024 restart points per round",
+                       "value": float(np.median(par2_32)), "unit": "s", "solved": sum(r.solved for r in runs32),
+                       "median_rounds": float(np.median([r.rounds for r in runs32]))},
         "roofline": None, "cpu_baseline": cpu,
         "e2e": {"value": float(np.median(e2e)), "unit": "s", "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
                 "note": "instance load (host preprocessing and upload) plus the solve"},
