@@ -766,7 +766,7 @@ def run_learned(args, rank: int, world: int, local_rank: int):
     # a family the CLS can solve within the budget, so that time-to-SAT is defined for both arms
     solvable = learned.learned_restart_experiment(
         train_count=600, test_count=24, n_train=400, n_test=350, family="3sat",
-        test_cfg=learned.CLSConfig(B=256, T=100, lr=0.1, max_rounds=300, seed=9))
+        test_cfg=learned.CLSConfig(B=256, T=100, lr=0.1, max_rounds=1000, seed=9))
     line = {
         "metric": "time-to-SAT (median s, PAR-2), learned vs uniform restarts", "value": res["median_par2_s"]["learned"],
         "unit": "s", "n_gpus": 1, "steps": res["test_instances"], "warmup": 0,
@@ -778,7 +778,7 @@ def run_learned(args, rank: int, world: int, local_rank: int):
         "uniform_par2_s": res["median_par2_s"]["uniform"], "experiment": res,
         "planted_3sat_n350": {k: solvable[k] for k in ("solved", "median_time_to_sat_s", "median_par2_s",
                                                        "median_rounds", "mean_best_unsat", "held_out_sign_agreement",
-                                                       "par2_budget_s")},
+                                                       "par2_budget_s", "median_par2_s_to_unsat_le", "test")},
         "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
     }
     print(json.dumps(line), flush=True)

@@ -10,7 +10,7 @@ from __future__ import annotations
 import math
 import time
 from dataclasses import dataclass, field
-from typing import List, Optional
+from typing import List, Optional, Tuple
 
 import numpy as np
 
@@ -189,6 +189,12 @@ class SatRun:
     seconds: float
     rounds: int
     best_unsat: int = -1  # fewest violated constraints of any point seen (0 when solved)
+    # (seconds since the start, fewest violated constraints so far) after every round
+    trajectory: List[Tuple[float, int]] = field(default_factory=list)
+
+    def time_to_unsat(self, k: int) -> float:
+        """Seconds until some point violated at most k constraints (inf if never)."""
+        return next((t for t, u in self.trajectory if u <= k), math.inf)
 
 
 def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optional[ffsat.MPNN] = None,
@@ -205,15 +211,16 @@ def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optio
     prop = None if net is None else net.forward(h)
     S = CLSSearch(h, n, cfg, seed, prop)
     best = None
+    traj = []
     for r in range(cfg.max_rounds):
         solved, nun = S.round(r)
         m = nun.min()
         best = m if best is None else torch.minimum(best, m)
-        if bool((m <= target_unsat).item()):
-            torch.cuda.synchronize()
-            return SatRun(True, time.perf_counter() - t0, r + 1, 0)
-    torch.cuda.synchronize()
-    return SatRun(False, time.perf_counter() - t0, cfg.max_rounds, int(best.item()) if best is not None else -1)
+        b = int(best.item())  # the round's one host synchronisation
+        traj.append((time.perf_counter() - t0, b))
+        if b <= target_unsat:
+            return SatRun(True, traj[-1][0], r + 1, 0, traj)
+    return SatRun(False, time.perf_counter() - t0, cfg.max_rounds, traj[-1][1] if traj else -1, traj)
 
 
 def time_to_sat_graph(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, target_unsat: int = 0,
@@ -270,6 +277,9 @@ def time_to_sat_graph(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, targ
     return SatRun(False, time.perf_counter() - t0, cfg.max_rounds, int(best.item()))
 
 
+UNSAT_LADDER = (400, 200, 100, 50, 20, 5, 0)
+
+
 @dataclass
 class ABResult:
     uniform: List[SatRun] = field(default_factory=list)
@@ -298,7 +308,16 @@ class ABResult:
             "median_rounds": {k: float(np.median([r.rounds for r in v])) for k, v in arms.items()},
             "solved": {k: sum(r.solved for r in v) for k, v in arms.items()},
             "mean_best_unsat": {k: float(np.mean([r.best_unsat for r in v])) for k, v in arms.items()},
+            # median (PAR-2) time until some point violates at most K constraints, for a
+            # fixed ladder of K: time-to-SAT is the K = 0 rung
+            "median_par2_s_to_unsat_le": {
+                str(K): {k: self._par2_to(v, K, budget) for k, v in arms.items()} for K in UNSAT_LADDER},
         }
+
+    @staticmethod
+    def _par2_to(runs, K, budget):
+        v = [min(r.time_to_unsat(K), 2.0 * budget) for r in runs]
+        return float(np.median(v)) if v else math.nan
 
 
 def warm(h: ffsat.Instance, n: int, cfg: CLSConfig, net: Optional[ffsat.MPNN]):
