@@ -80,6 +80,17 @@ typedef struct ffsat_options {
     int32_t autotune;
     /* CUDA device ordinal, -1 = the current device. */
     int32_t device;
+    /* CTAs per point of FP64 fixed-step calls (ffsat_step, ffsat_step_noalloc)
+     * whose x and gradient fit in shared memory: 0 = automatic (a thread-block
+     * cluster of 8, 4 or 2 CTAs when B clusters of that size fit on the GPU at
+     * once and every CTA gets at least two warp tasks; GB300's FP64 rate is far
+     * below its FP32 rate, so a few points otherwise leave most SMs' FP64 pipes
+     * idle), 1 = one CTA per point, 2, 4 or 8 = that cluster size whenever a
+     * cluster of it fits on the GPU.  The CTAs of a cluster split the point's
+     * warp tasks and combine their partial gradients through distributed
+     * shared memory (the sum of the partials, in rank order, replaces one
+     * floating-point accumulation order by another). */
+    int32_t cluster;
 } ffsat_options;
 
 typedef struct ffsat_step_args {
@@ -381,6 +392,10 @@ int ffsat_instance_info(const ffsat_instance *inst, ffsat_info *info);
 
 /* Number of kernel launches the last eval/step/check call on this thread enqueued. */
 int32_t ffsat_last_launch_count(void);
+
+/* CTAs per point of the last ffsat_step / ffsat_step_noalloc call on this
+ * thread (1 unless it ran one thread-block cluster per point; 0 before any). */
+int32_t ffsat_last_cluster_size(void);
 
 /* Message for the last error on this thread ("" if none). */
 const char *ffsat_last_error(void);

@@ -1,0 +1,216 @@
+// FP64 projected-GD step with one thread-block cluster per point.
+//
+// GB300 executes FP64 far below its FP32 rate, so an FP64 step whose points
+// occupy only a few SMs is bound by the FP64 pipes of those SMs.  This kernel
+// gives each point a cluster of CL CTAs on CL SMs (CL = 2, 4 or 8):
+//
+//   * every CTA holds the point's x in its shared memory and evaluates the warp
+//     tasks r, r + CL, r + 2 CL, ... (r = its rank in the cluster) into its own
+//     gradient buffer;
+//   * the cluster barrier (release / acquire) makes the CL partial gradients
+//     visible to the whole cluster;
+//   * every CTA sums the CL partials of each variable in rank order through
+//     distributed shared memory and takes the same step
+//     x <- clip(x - lr g, -1, 1) on its own copy, so the copies stay identical.
+//
+// Two gradient buffers alternate between iterations: the buffer a CTA clears
+// after the barrier of iteration k was last read by its peers before that
+// barrier, so one cluster barrier per iteration suffices.  After the last
+// iteration a final cluster barrier ends all remote reads; rank 0 alone then
+// runs the exact check, the violation counts, the restart and the write-back.
+// Fixed-step mode only (the line search needs F on every trial).
+#pragma once
+#include "fused_launch.cuh"
+
+namespace ffsat {
+namespace dev {
+
+__device__ __forceinline__ int cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return (int)r;
+}
+__device__ __forceinline__ int cluster_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return (int)r;
+}
+__device__ __forceinline__ int cluster_index() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return (int)r;
+}
+
+// Every thread of every CTA of the cluster; shared-memory writes before it are
+// visible to distributed shared-memory reads after it.
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Element v of the shared array `local` as held by CTA `rank` of the cluster.
+__device__ __forceinline__ double ld_peer(const double *local, int v, int rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(local + v);
+    uint32_t ra;
+    double x;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(x) : "r"(ra) : "memory");
+    return x;
+}
+
+// The warp tasks t with t mod CL = rank, pulled in order from the CTA's counter;
+// gradient contributions go to G.  Starts and ends with a CTA barrier.
+template <typename R, int NR, int NI, int XG, typename Acc>
+__device__ __forceinline__ void eval_tasks_strided(const DevView &V, const Src &S, const R *xrow, const Acc &G,
+                                                   int &s_ctr, int rank, int CL) {
+    constexpr bool SF = false;  // FP64 node factors are recomputed in the prefix pass
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_ctr = 0;
+    __syncthreads();
+    R facc = R(0);  // the objective is not needed by a fixed-step call
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&s_ctr, 1);
+        t = __shfl_sync(kFull, t, 0) * CL + rank;
+        if (t >= V.n_task) break;
+        const int4 task = S.tasks[t];
+        const int kind = task.x & 0xff;
+        const bool xr = kind == TASK_XOR2;
+        if (kind == TASK_CLAUSE || xr) {
+            if (task.z == 128) {
+                if (xr) clause_task<R, XG, 4, true>(V, S, task, lane, xrow, G, true, facc);
+                else clause_task<R, XG, 4, false>(V, S, task, lane, xrow, G, true, facc);
+            } else if (task.z == 64) {
+                if (xr) clause_task<R, XG, 2, true>(V, S, task, lane, xrow, G, true, facc);
+                else clause_task<R, XG, 2, false>(V, S, task, lane, xrow, G, true, facc);
+            } else {
+                if (xr) clause_task<R, XG, 1, true>(V, S, task, lane, xrow, G, true, facc);
+                else clause_task<R, XG, 1, false>(V, S, task, lane, xrow, G, true, facc);
+            }
+        } else if (kind == TASK_PROD) {
+            prod_task<R, XG>(V, S, task, lane, xrow, G, true, facc);
+        } else {
+            const int nr = (task.x >> 16) & 0xff;
+            if constexpr (NR >= 16) {
+                if (nr == 12)
+                    node_task<R, 12, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
+                else if (nr == 8)
+                    node_task<R, 8, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
+                else
+                    node_task<R, 16, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
+            } else if constexpr (NR > 0) {
+                node_task<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Shared memory: x | gradient buffer 0 | resident image (SMEM_RES) as in the
+// one-CTA kernel, and gradient buffer 1 at byte offset g1_off.
+template <typename R, int NR, int NI, int SM, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1) fused_cluster_kernel(const DevView V, const FusedArgs A,
+                                                                   unsigned g1_off) {
+    static_assert(sizeof(R) == 8 && (SM == SMEM_FULL || SM == SMEM_RES), "FP64, x and gradient in shared memory");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ BlockShared sh;
+    const Src S = make_src<R, SM, THREADS>(V, smem_raw, true);
+    const int CL = cluster_count(), rank = cluster_rank(), b = cluster_index();
+    if (b >= A.B) return;  // the whole cluster leaves together
+    const int n = V.n;
+    const int npad = (n + 2 + 3) & ~3;
+    const int tid = threadIdx.x;
+    R *xs = reinterpret_cast<R *>(smem_raw);
+    R *const g0 = xs + npad;
+    R *const g1 = reinterpret_cast<R *>(smem_raw + g1_off);
+    const R *x_in = static_cast<const R *>(A.x_in);
+    R *x_out = static_cast<R *>(A.x_out);
+    const size_t rowoff = (size_t)b * (size_t)n;
+    bool bad = false;
+    for (int v = tid; v < n; v += THREADS) {
+        const R xv = x_in[rowoff + v];
+        bad |= isnan(xv);
+        xs[v] = xv;
+    }
+    if (tid == 0) {
+        xs[n] = R(1);
+        xs[n + 1] = R(0);
+    }
+    if (bad && rank == 0) atomicOr(V.status, STATUS_NAN);
+    for (int v = tid; v < npad; v += THREADS) {
+        g0[v] = R(0);
+        g1[v] = R(0);
+    }
+    const R lr = R(A.sp.lr);
+    for (int it = 0; it < A.sp.T; ++it) {
+        R *const gw = (it & 1) ? g1 : g0;
+        R *const gz = (it & 1) ? g0 : g1;
+        PlainAcc<R> G;
+        G.g = gw;
+        eval_tasks_strided<R, NR, NI, SMEM_FULL>(V, S, xs, G, sh.ctr, rank, CL);
+        cluster_barrier();
+        for (int v = tid; v < n; v += THREADS) {
+            R g = R(0);
+            for (int q = 0; q < CL; ++q) g += ld_peer(gw, v, q);
+            R z = xs[v] - lr * g;
+            z = z < R(-1) ? R(-1) : (z > R(1) ? R(1) : z);
+            xs[v] = z;
+            gz[v] = R(0);
+        }
+        // the next evaluation starts with a CTA barrier
+    }
+    cluster_barrier();  // no peer reads this CTA's buffers after this point
+    if (rank != 0) return;
+    __syncthreads();
+    const int unsat = block_unsat<R>(V, xs, sh.ired, A.unsat_counts);
+    if (tid == 0) sh.ired[0] = unsat;
+    __syncthreads();
+    const int u = sh.ired[0];
+    if (tid == 0) {
+        if (A.solved) A.solved[b] = (uint8_t)(u == 0);
+        if (A.n_unsat) A.n_unsat[b] = u;
+    }
+    if (u != 0 && A.sp.restart) {
+        const uint64_t kb = splitmix64(splitmix64(splitmix64(A.sp.seed) ^ A.sp.epoch) ^ (A.sp.b_offset + (uint64_t)b));
+        for (int v = tid; v < n; v += THREADS) xs[v] = restart_value<R>(kb, (uint64_t)v);
+    }
+    for (int v = tid; v < n; v += THREADS) x_out[rowoff + v] = xs[v];
+}
+
+template <typename R, int NR, int SM>
+cudaError_t cluster_launch_mode(const DevView &V, const FusedArgs &a, size_t smem, size_t g1_off, int B, int CL,
+                                cudaStream_t s, int *max_active) {
+    constexpr int TH = fused_threads(true, NR);
+    auto k = fused_cluster_kernel<R, NR, node_interleave<R, NR>(), SM, TH>;
+    cudaError_t e = raise_smem_limit(k, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)B * (unsigned)CL);
+    cfg.blockDim = dim3(TH);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    if (max_active) return cudaOccupancyMaxActiveClusters(max_active, k, &cfg);
+    e = cudaLaunchKernelEx(&cfg, k, V, a, (unsigned)g1_off);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+template <typename R, int NR>
+cudaError_t cluster_launch(const DevView &V, int smem_mode, const FusedArgs &a, size_t smem, size_t g1_off, int B,
+                           int CL, cudaStream_t s, int *max_active) {
+    if (smem_mode == SMEM_RES) return cluster_launch_mode<R, NR, SMEM_RES>(V, a, smem, g1_off, B, CL, s, max_active);
+    return cluster_launch_mode<R, NR, SMEM_FULL>(V, a, smem, g1_off, B, CL, s, max_active);
+}
+
+}  // namespace dev
+}  // namespace ffsat
+
+#define FFSAT_DEFINE_CLUSTER(name, NR)                                                                       \
+    namespace ffsat {                                                                                        \
+    FFSAT_CLUSTER_LAUNCHER(name) { return dev::cluster_launch<double, NR>(V, smem_mode, a, smem, g1_off, B, CL, s, max_active); } \
+    }

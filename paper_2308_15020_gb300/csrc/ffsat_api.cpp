@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "ffsat.h"
+#include "cluster_launch.h"
 #include "ffsat_internal.h"
 #include "heuristics.h"
 
@@ -23,6 +24,7 @@ namespace {
 
 thread_local std::string t_err;
 thread_local int32_t t_launches = 0;
+thread_local int32_t t_cluster = 0;
 
 int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -172,6 +174,8 @@ struct ffsat_instance {
     void *d_yscratch = nullptr;  // extrapolated points of ffsat_step_pgfp
     size_t yscratch_bytes = 0;
     ffsat_info info{};
+    // resident clusters of the FP64 cluster step for CL = 2, 4, 8 (-1: not asked yet)
+    int cluster_active[3] = {-1, -1, -1};
     // learned-proposal graph data (built on first use)
     unsigned char *d_graph = nullptr;
     GraphView graph{};
@@ -185,6 +189,8 @@ int validate(int32_t n, int32_t m, const int64_t *rp, const int32_t *lits, const
     if (m < 0) return fail(FFSAT_ERR_ARG, "n_cons must be >= 0 (got %d)", m);
     if (o.form != FFSAT_FORM_STABLE && o.form != FFSAT_FORM_PAPER) return fail(FFSAT_ERR_ARG, "bad form %d", o.form);
     if (o.node_r != 0 && o.node_r != 8 && o.node_r != 16) return fail(FFSAT_ERR_ARG, "node_r must be 0, 8 or 16");
+    if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4 && o.cluster != 8)
+        return fail(FFSAT_ERR_ARG, "cluster must be 0, 1, 2, 4 or 8");
     if (!rp) return fail(FFSAT_ERR_ARG, "row_ptr is NULL");
     if (m > 0 && (!type || !param)) return fail(FFSAT_ERR_ARG, "type/param is NULL");
     if (rp[0] != 0) return fail(FFSAT_ERR_PARAM, "row_ptr[0] must be 0");
@@ -878,11 +884,14 @@ void ffsat_default_options(ffsat_options *opt) {
     opt->node_r = 0;
     opt->autotune = 0;
     opt->device = -1;
+    opt->cluster = 0;
 }
 
 const char *ffsat_last_error(void) { return t_err.c_str(); }
 
 int32_t ffsat_last_launch_count(void) { return t_launches; }
+
+int32_t ffsat_last_cluster_size(void) { return t_cluster; }
 
 int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, const int32_t *lits,
                         const uint8_t *type, const int32_t *param, const double *weights,
@@ -1222,6 +1231,58 @@ static int check_dtype(int32_t dtype) {
 
 static inline int grid_for(int32_t B) { return B; }
 
+using ClusterFn = cudaError_t (*)(const DevView &, int, const FusedArgs &, size_t, size_t, int, int, cudaStream_t,
+                                  int *);
+
+static ClusterFn cluster_launcher(int nr) {
+    return nr == 0 ? cluster_f64_r0 : (nr == 8 ? cluster_f64_r8 : cluster_f64_r16);
+}
+
+// CTAs per point for an FP64 fixed-step call on B points (ffsat_options.cluster):
+// 1 for the one-CTA kernel, else the cluster size, with the cluster kernel's
+// dynamic shared memory and the offset of its second gradient buffer.
+static int step_cluster_size(ffsat_instance *I, int32_t B, int mode, size_t &smem, size_t &g1_off) {
+    const int opt = I->opt.cluster;
+    if (opt == 1 || (mode != SMEM_FULL && mode != SMEM_RES)) return 1;
+    const size_t npad = ((size_t)I->n + 2 + 3) & ~size_t(3);
+    g1_off = (I->smem64 + 15) & ~size_t(15);
+    smem = g1_off + npad * sizeof(double);
+    if (smem + 1024 > (size_t)I->max_smem) return 1;
+    static const int sizes[3] = {2, 4, 8};
+    for (int k = 2; k >= 0; --k) {
+        const int cl = sizes[k];
+        if (opt != 0 && cl != opt) continue;
+        if (opt == 0 && ((int64_t)B * cl > I->num_sms || I->V64.n_task < 2 * cl)) continue;
+        if (I->cluster_active[k] < 0) {
+            int active = 0;
+            if (cluster_launcher(I->nr64)(I->V64, mode, FusedArgs{}, smem, g1_off, 1, cl, nullptr, &active) !=
+                cudaSuccess) {
+                (void)cudaGetLastError();
+                active = 0;
+            }
+            I->cluster_active[k] = active;
+        }
+        if (I->cluster_active[k] >= (opt == 0 ? B : 1)) return cl;
+    }
+    return 1;
+}
+
+// The fused step launch of ffsat_step and ffsat_step_noalloc.
+static int launch_step(ffsat_instance *I, bool f64, int mode, const FusedArgs &a, int32_t B, void *stream) {
+    const DevView &V = f64 ? I->V64 : I->V32;
+    size_t csmem = 0, g1_off = 0;
+    const int cl = f64 ? step_cluster_size(I, B, mode, csmem, g1_off) : 1;
+    if (cl > 1)
+        CUDA_TRY(cluster_launcher(I->nr64)(V, mode, a, csmem, g1_off, B, cl, static_cast<cudaStream_t>(stream),
+                                           nullptr));
+    else
+        CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(B),
+                                                              static_cast<cudaStream_t>(stream), false));
+    t_cluster = cl;
+    t_launches = 1;
+    return FFSAT_OK;
+}
+
 int ffsat_eval_grad(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, double *f, void *g, void *stream) {
     t_err.clear();
     t_launches = 0;
@@ -1267,6 +1328,7 @@ int ffsat_step(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat
                int32_t *n_unsat, void *stream) {
     t_err.clear();
     t_launches = 0;
+    t_cluster = 1;
     if (!I || !args) return fail(FFSAT_ERR_ARG, "NULL argument");
     if (B < 0 || args->T < 0) return fail(FFSAT_ERR_ARG, "B and T must be >= 0");
     if (!std::isfinite(args->lr)) return fail(FFSAT_ERR_ARG, "lr must be finite");
@@ -1303,17 +1365,14 @@ int ffsat_step(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat
         }
         a.g_scratch = I->d_scratch;
     }
-    const DevView &V = f64 ? I->V64 : I->V32;
-    CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(B),
-                                                          static_cast<cudaStream_t>(stream), false));
-    t_launches = 1;
-    return FFSAT_OK;
+    return launch_step(I, f64, mode, a, B, stream);
 }
 
 int ffsat_step_noalloc(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat_step_args *args,
                        uint8_t *solved, int32_t *n_unsat, void *stream) {
     t_err.clear();
     t_launches = 0;
+    t_cluster = 1;
     if (!I || !args) return fail(FFSAT_ERR_ARG, "NULL argument");
     if (B < 0 || args->T < 0) return fail(FFSAT_ERR_ARG, "B and T must be >= 0");
     if (!std::isfinite(args->lr)) return fail(FFSAT_ERR_ARG, "lr must be finite");
@@ -1348,11 +1407,7 @@ int ffsat_step_noalloc(ffsat_instance *I, int32_t B, void *x, int32_t dtype, con
         CUDA_TRY(static_scratch(I->device, &p));
         a.g_scratch = p;
     }
-    const DevView &V = f64 ? I->V64 : I->V32;
-    CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(B),
-                                                          static_cast<cudaStream_t>(stream), false));
-    t_launches = 1;
-    return FFSAT_OK;
+    return launch_step(I, f64, mode, a, B, stream);
 }
 
 static int grow_scratch(void **p, size_t *have, size_t need) {

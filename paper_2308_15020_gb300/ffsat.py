@@ -70,6 +70,7 @@ SYMBOLS = (
     "ffsat_sync_status",
     "ffsat_instance_info",
     "ffsat_last_launch_count",
+    "ffsat_last_cluster_size",
     "ffsat_last_error",
     "ffsat_free",
 )
@@ -106,7 +107,7 @@ class FFSatError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("form", C.c_int32), ("node_all", C.c_int32), ("node_r", C.c_int32), ("autotune", C.c_int32),
-                ("device", C.c_int32)]
+                ("device", C.c_int32), ("cluster", C.c_int32)]
 
 
 class StepArgs(C.Structure):
@@ -218,6 +219,8 @@ def lib():
         L.ffsat_instance_info.restype = C.c_int
         L.ffsat_last_launch_count.argtypes = []
         L.ffsat_last_launch_count.restype = C.c_int32
+        L.ffsat_last_cluster_size.argtypes = []
+        L.ffsat_last_cluster_size.restype = C.c_int32
         L.ffsat_last_error.argtypes = []
         L.ffsat_last_error.restype = C.c_char_p
         L.ffsat_free.argtypes = [_vp]
@@ -233,6 +236,11 @@ def _check(rc: int):
 
 def last_launch_count() -> int:
     return int(lib().ffsat_last_launch_count())
+
+
+def last_cluster_size() -> int:
+    """CTAs per point of the last step call on this thread (1: one CTA per point)."""
+    return int(lib().ffsat_last_cluster_size())
 
 
 def _ptr(t) -> Optional[int]:
@@ -266,7 +274,7 @@ class Instance:
     """An instance loaded into the library (``ffsat_load_instance``)."""
 
     def __init__(self, inst, form: int = FFSAT_FORM_STABLE, node_all: bool = False, node_r: int = 0,
-                 autotune: bool = False, device: int = -1):
+                 autotune: bool = False, device: int = -1, cluster: int = 0):
         import numpy as np
 
         self.n = int(inst.n)
@@ -279,6 +287,7 @@ class Instance:
         opt = Options()
         lib().ffsat_default_options(C.byref(opt))
         opt.form, opt.node_all, opt.node_r, opt.autotune, opt.device = form, int(node_all), node_r, int(autotune), device
+        opt.cluster = cluster
         h = _vp()
         rc = lib().ffsat_load_instance(self.n, self.m, self._rp.ctypes.data, self._lits.ctypes.data,
                                        self._ty.ctypes.data, self._pa.ctypes.data, self._w.ctypes.data,

@@ -37,7 +37,7 @@ def test_exports_every_declared_symbol(F):
 def test_default_options(F):
     o = F.Options()
     F.lib().ffsat_default_options(C.byref(o))
-    assert (o.form, o.node_all, o.node_r, o.autotune, o.device) == (0, 0, 0, 0, -1)
+    assert (o.form, o.node_all, o.node_r, o.autotune, o.device, o.cluster) == (0, 0, 0, 0, -1, 0)
 
 
 def _load(F, n, rp, lits, ty, pa, w=None, **opt):
@@ -75,6 +75,7 @@ def _load(F, n, rp, lits, ty, pa, w=None, **opt):
     (dict(n=600, rp=[0, 513], lits=list(range(1, 514)), ty=[2], pa=[3]), -7),  # longer than 512
     (dict(n=100, rp=[0, 61], lits=list(range(1, 62)), ty=[2], pa=[3], form=1), -7),  # paper form > 60
     (dict(n=3, rp=[0, 2], lits=[1, 2], ty=[0], pa=[0], node_r=5), -1),        # bad option
+    (dict(n=3, rp=[0, 2], lits=[1, 2], ty=[0], pa=[0], cluster=3), -1),       # cluster size not 0/1/2/4/8
 ])
 def test_validation_codes(F, case, code):
     rc, msg = _load(F, case.pop("n"), case.pop("rp"), case.pop("lits"), case.pop("ty"), case.pop("pa"),
