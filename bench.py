@@ -834,6 +834,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize()
     h.sync_status()
     launches_per_step = ffsat.last_launch_count()
+    ctas_per_point = ffsat.last_cluster_size()
     time.sleep(0.5)
 
     # ---- device-timed region ----
@@ -941,7 +942,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": dtname, "data": "synthetic (seeded generator)",
         "config": {"workload": args.workload, "B": B, "n": inst.n, "m": inst.m, "nnz": inst.nnz,
-                   "pgd_iters_per_step": T, "lr": lr, "form": "stable",
+                   "pgd_iters_per_step": T, "lr": lr, "form": "stable", "ctas_per_point": ctas_per_point,
                    "l2": "flushed before every timed step (256 MiB write)",
                    "parallelism": f"replicas x{world} (points sharded, no collective)"},
         "roofline": roof,
