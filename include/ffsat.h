@@ -83,7 +83,7 @@ typedef struct ffsat_options {
     /* CTAs per point of FP64 fixed-step calls (ffsat_step, ffsat_step_noalloc)
      * whose x and gradient fit in shared memory: 0 = automatic (a thread-block
      * cluster of 8, 4 or 2 CTAs when B clusters of that size fit on the GPU at
-     * once and every CTA gets at least two warp tasks; GB300's FP64 rate is far
+     * once and every CTA gets at least one warp task; GB300's FP64 rate is far
      * below its FP32 rate, so a few points otherwise leave most SMs' FP64 pipes
      * idle), 1 = one CTA per point, 2, 4 or 8 = that cluster size whenever a
      * cluster of it fits on the GPU.  The CTAs of a cluster split the point's

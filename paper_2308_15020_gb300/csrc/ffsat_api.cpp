@@ -1248,11 +1248,14 @@ static int step_cluster_size(ffsat_instance *I, int32_t B, int mode, size_t &sme
     g1_off = (I->smem64 + 15) & ~size_t(15);
     smem = g1_off + npad * sizeof(double);
     if (smem + 1024 > (size_t)I->max_smem) return 1;
+    // more than half of an SM's shared memory: one CTA per SM, so that the CTAs of
+    // the clusters do not share an SM's FP64 pipe while other SMs idle
+    smem = std::max(smem, (size_t)I->max_smem / 2 + 1024);
     static const int sizes[3] = {2, 4, 8};
     for (int k = 2; k >= 0; --k) {
         const int cl = sizes[k];
         if (opt != 0 && cl != opt) continue;
-        if (opt == 0 && ((int64_t)B * cl > I->num_sms || I->V64.n_task < 2 * cl)) continue;
+        if (opt == 0 && ((int64_t)B * cl > I->num_sms || I->V64.n_task < cl)) continue;
         if (I->cluster_active[k] < 0) {
             int active = 0;
             if (cluster_launcher(I->nr64)(I->V64, mode, FusedArgs{}, smem, g1_off, 1, cl, nullptr, &active) !=
