@@ -60,14 +60,19 @@ NODE_FLOPS = 19
 CLOSED_FLOPS = 5
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(family: str = "fused") -> str:
     """Hash of the device-code sources of the fused step kernel (and the batch
-    kernel built from the same body; the host-side launcher is left out): a
-    committed ncu summary applies while this matches."""
+    kernel built from the same body; the host-side launcher is left out), or with
+    family "cluster" of the one-cluster-per-point step kernel and the task bodies
+    it shares: a committed ncu summary applies while this matches."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2308_15020_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        if f.startswith("fused_") and f != "fused_launch.cuh" or f in ("batch_kernels.cu", "ffsat_internal.h"):
+        if family == "cluster":
+            take = f in ("cluster_step.cuh", "fused_kernel.cuh", "ffsat_internal.h")
+        else:
+            take = f.startswith("fused_") and f != "fused_launch.cuh" or f in ("batch_kernels.cu", "ffsat_internal.h")
+        if take:
             with open(os.path.join(csrc, f), "rb") as fh:
                 h.update(f.encode() + fh.read())
     return h.hexdigest()[:16]
@@ -83,7 +88,7 @@ def profile_traffic(kernel: str, workload: str):
         if ":" in line:
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("kernel_source_hash") != kernel_source_hash():
+    if vals.get("kernel_source_hash") != kernel_source_hash("cluster" if kernel == "ffsat_cluster" else "fused"):
         return None
     try:
         return float(vals["dram_bytes_per_launch_full"])
@@ -930,7 +935,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         achieved = bytes_ / launch_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_per_launch": bytes_}
-    roof["traffic"] = profile_traffic("ffsat_fused", args.workload)
+    roof["traffic"] = profile_traffic("ffsat_cluster" if ctas_per_point > 1 else "ffsat_fused", args.workload)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
