@@ -96,6 +96,25 @@ def profile_traffic(kernel: str, workload: str):
         return None
 
 
+NCU_COUNTERS = {"issue active %": "issue_active_pct", "FMA pipe %": "fma_pipe_pct",
+                "shared/L1 wavefronts % of peak": "shared_wavefronts_pct_of_peak",
+                "FP64 pipe % (avg / max over SMs)": "fp64_pipe_pct_avg_max", "warps active / SM": "warps_active_per_sm"}
+
+
+def profile_counters(kernel: str, workload: str):
+    """Utilisation counters of the committed ncu summary for the kernel and
+    workload (the same capture as profile_traffic), if it matches the source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if profile_traffic(kernel, workload) is None:
+        return None
+    out = {}
+    for line in open(path):
+        for label, key in NCU_COUNTERS.items():
+            if line.strip().startswith(label):
+                out[key] = line.strip()[len(label):].strip()
+    return out or None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -942,7 +961,9 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         achieved = bytes_ / launch_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_per_launch": bytes_}
-    roof["traffic"] = profile_traffic("ffsat_cluster" if ctas_per_point > 1 else "ffsat_fused", args.workload)
+    prof_kernel = "ffsat_cluster" if ctas_per_point > 1 else "ffsat_fused"
+    roof["traffic"] = profile_traffic(prof_kernel, args.workload)
+    roof["ncu"] = profile_counters(prof_kernel, args.workload)
 
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -1082,7 +1103,8 @@ def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
     roof = {"bound": "alu", "achieved": flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
             "frac": flops / launch_s / 1e12 / peak,
             "peak_source": f"FP32 FMA lanes x 2 x {sm_max:.0f} MHz (max SM clock, {peak_src} peaks file)",
-            "algorithmic_per_launch": flops, "traffic": profile_traffic("ffsat_batch", args.workload)}
+            "algorithmic_per_launch": flops, "traffic": profile_traffic("ffsat_batch", args.workload),
+            "ncu": profile_counters("ffsat_batch", args.workload)}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_batch(insts, B, T, lr, target_s=args.cpu_seconds)
