@@ -178,7 +178,8 @@ int ffsat_eval_grad_plain64(ffsat_instance *inst, int32_t B, const double *x, do
  * x <- clip(x - lr grad F(x), -1, 1) (App. A.3 with a fixed step), then the exact
  * check of sgn(x) (sgn(x) = -1 iff x < 0), then, if args->restart, a uniform
  * redraw of every point that is not a model.  All iterations run inside one
- * kernel launch per call.
+ * kernel launch per call (FP64 calls on few points: one thread-block cluster
+ * per point, see ffsat_options.cluster).
  *   x: device [B, n] of dtype, updated in place;
  *   solved: device [B] uint8 (1 iff sgn(x) satisfies every constraint), or NULL;
  *   n_unsat: device [B] int32 (violated constraints at sgn(x) before any restart), or NULL. */
