@@ -24,6 +24,7 @@ import hashlib
 import math
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -251,9 +252,37 @@ def calibrate_sample(inst, n_total_pts: int, T: int, lr: float, target_s: float)
     return B_s, T_s
 
 
+def host_cpu_model() -> str:
+    """The host CPU's model name as lscpu reports it."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
+
+
+def single_thread_rate(inst, T: int, lr: float, target_s: float = 1.0):
+    """literal-grads/s of the FP64 oracle's round on one point and one thread."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    x1 = gen.uniform_points(1, inst.n, 98, dtype=np.float64)
+    t0 = time.perf_counter()
+    O.step(inst, x1, T=1, lr=lr, seed=0, restart=False, nthreads=1)
+    per_iter = max(time.perf_counter() - t0, 1e-6)
+    T1 = int(max(1, min(T, target_s / per_iter)))
+    t0 = time.perf_counter()
+    O.step(inst, x1, T=T1, lr=lr, seed=0, restart=False, nthreads=1)
+    return inst.nnz * T1 / (time.perf_counter() - t0)
+
+
 def cpu_baseline(inst, B: int, T: int, lr: float, target_s: float = 12.0):
     """The FP64 oracle's projected-GD round on a bounded sample of the workload,
-    repeated until about target_s seconds of host time have been spent."""
+    repeated until about target_s seconds of host time have been spent (all host
+    threads, OpenMP over points), and on one point with one thread."""
     B_s, T_s = calibrate_sample(inst, B, T, lr, target_s)
     xs = gen.uniform_points(B_s, inst.n, 0, dtype=np.float64)
     reps, total = 0, 0.0
@@ -264,7 +293,8 @@ def cpu_baseline(inst, B: int, T: int, lr: float, target_s: float = 12.0):
     rate = reps * B_s * inst.nnz * T_s / total
     return {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{B_s} of {B} points x {T_s} of {T} PGD iterations, run {reps} time(s), FP64 oracle, "
-                      f"{total:.1f} s"}
+                      f"{total:.1f} s",
+            "single_thread_value": single_thread_rate(inst, T, lr), "cpu_model": host_cpu_model()}
 
 
 def cpu_baseline_batch(insts, B: int, T: int, lr: float, target_s: float = 12.0):
@@ -362,7 +392,8 @@ def run_reference(args, rank: int, world: int):
         "config": {"workload": args.workload, "B": B, "n": inst.n, "m": inst.m, "nnz": inst.nnz,
                    "pgd_iters_per_step": T, "lr": lr, "parallelism": "host threads"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": f"{B_s} of {B} points x {T_s} of {T} PGD iterations per step, FP64 oracle"},
+                         "sample": f"{B_s} of {B} points x {T_s} of {T} PGD iterations per step, FP64 oracle",
+                         "cpu_model": host_cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
