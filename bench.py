@@ -49,6 +49,10 @@ WORKLOADS = {
     "uneven_batch": (gen.uneven_batch, 128, "f32", 2, 0.1),
 }
 
+# timed steps when --steps is not given: a timed region of a few hundred
+# milliseconds, so that the clock sampler sees it several times
+DEFAULT_STEPS = {"cnf_xor_n2000": 100, "3sat_n100": 200, "cnf_card_n20000": 10, "uneven_batch": 3}
+
 FP32_LANES_PER_SM = 128
 # shared memory: 32 banks x 4 bytes per clock per SM
 SMEM_BYTES_PER_CLK_SM = 128
@@ -172,7 +176,7 @@ class ClockSampler:
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu=timestamp,{self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                          "--format=csv,noheader,nounits", "-lms", "50"], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -198,7 +202,7 @@ class ClockSampler:
                 ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
             except ValueError:
                 ts = self.t_mark
-            if ts < self.t_mark - 0.25:
+            if ts < self.t_mark - 0.05:
                 continue
             try:
                 sm.append(float(parts[2]))
@@ -375,7 +379,8 @@ def run_reference(args, rank: int, world: int):
     inst = build(0)
     if isinstance(inst, list):  # a batch workload: time the median instance
         inst = inst[len(inst) // 2]
-    B_s, T_s = calibrate_sample(inst, B, T, lr, target_s=args.ref_seconds)
+    # each step a bounded sample, so that the whole run stays near two minutes for any K
+    B_s, T_s = calibrate_sample(inst, B, T, lr, target_s=min(args.ref_seconds, 120.0 / max(1, args.steps)))
     xs = gen.uniform_points(B_s, inst.n, 0, dtype=np.float64)
     for _ in range(args.warmup):
         oracle_rate(inst, xs, max(1, T_s // 4), lr)
@@ -1162,7 +1167,8 @@ def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=0,
+                    help="timed steps (0 = the workload's default: enough for several clock samples)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cnf_xor_n2000",
@@ -1180,6 +1186,8 @@ def main():
     ap.add_argument("--no-plain64", action="store_true",
                     help="skip the FP32-fused vs plain-FP64-GPU single-evaluation comparison")
     args = ap.parse_args()
+    if args.steps <= 0:
+        args.steps = DEFAULT_STEPS.get(args.workload, 20) if args.impl == "ours" else 20
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
