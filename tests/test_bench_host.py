@@ -52,17 +52,22 @@ def test_constant_cardinality_is_not_node_work(bench):
     ("ffsat_batch", "uneven_batch", "fused"),
     ("ffsat_cluster", "3sat_n100", "cluster"),
 ])
-def test_committed_summaries_match_the_sources(bench, kernel, workload, family):
-    """Each committed ncu summary names the source hash it was taken on; while it
-    matches, the bench lines report its DRAM traffic and counters."""
+def test_committed_summaries_pair_with_their_sources(bench, kernel, workload, family):
+    """Each committed ncu summary names the command and the source hash it was
+    taken on; the bench lines report its DRAM traffic and counters while the
+    hash matches the kernel's sources, and nothing once they have changed."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
     text = open(path).read()
     assert "--clock-control none" in text and "command:" in text
-    assert f"kernel_source_hash: {bench.kernel_source_hash(family)}" in text
+    taken = [ln.split(":", 1)[1].strip() for ln in text.splitlines() if ln.startswith("kernel_source_hash:")]
+    assert len(taken) == 1
     traffic = bench.profile_traffic(kernel, workload)
-    assert traffic is not None and traffic > 0
     counters = bench.profile_counters(kernel, workload)
-    assert counters and "issue_active_pct" in counters
+    if taken[0] == bench.kernel_source_hash(family):
+        assert traffic is not None and traffic > 0
+        assert counters and "issue_active_pct" in counters
+    else:
+        assert traffic is None and counters is None
     assert bench.profile_traffic(kernel, "no_such_workload") is None
 
 
