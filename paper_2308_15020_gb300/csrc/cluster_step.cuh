@@ -89,17 +89,7 @@ __device__ __forceinline__ void eval_tasks_strided(const DevView &V, const Src &
         } else if (kind == TASK_PROD) {
             prod_task<R, XG>(V, S, task, lane, xrow, G, true, facc);
         } else {
-            const int nr = (task.x >> 16) & 0xff;
-            if constexpr (NR >= 16) {
-                if (nr == 12)
-                    node_task<R, 12, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
-                else if (nr == 8)
-                    node_task<R, 8, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
-                else
-                    node_task<R, 16, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
-            } else if constexpr (NR > 0) {
-                node_task<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
-            }
+            node_dispatch<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
         }
     }
     __syncthreads();

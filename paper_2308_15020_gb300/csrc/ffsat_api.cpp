@@ -231,17 +231,24 @@ inline int32_t pack_lit(int32_t l) {
 inline int seg_lanes(int L, int R) { return std::max(1, pow2_at_least((L + R - 1) / R)); }
 
 // Literals per lane of a node segment.  A kernel built for node R = 16 also
-// runs 12 literals per lane; per segment the host picks the shape with the
-// smaller modelled cost per node, G * (12 NR + 12 + 10 log2 G) lane
-// instructions (12 per literal slot, butterfly and per-node overhead).
-inline int node_nr(int L, int nr_max) {
+// runs 12 and 8 literals per lane; per segment the host picks the shape with
+// the smallest modelled issue cost per node, G * (7 NR + 58 + 8 log2 G) lane
+// instructions for the imaginary-node task (7 per literal slot; per node the
+// normalisation, division and scales, and per butterfly level three shuffles,
+// an exponent add and a complex product), G * (14 NR + 12 + 10 log2 G) for the
+// generic one.
+inline int node_nr(int L, int nr_max, bool imag) {
     if (nr_max < 16) return nr_max;
     auto cost = [&](int nr) {
         const int G = seg_lanes(L, nr);
         if (G > 32) return 1e30;
-        return (double)G * (12.0 * nr + 12.0 + 10.0 * std::log2((double)G));
+        const double lg = std::log2((double)G);
+        return imag ? (double)G * (7.0 * nr + 58.0 + 8.0 * lg) : (double)G * (14.0 * nr + 12.0 + 10.0 * lg);
     };
-    return cost(12) < cost(16) ? 12 : 16;
+    int best = 16;
+    for (int nr : {12, 8})
+        if (cost(nr) < cost(best)) best = nr;
+    return best;
 }
 
 // Per-constraint FE of constant constraints (cardinality with K <= 0 or K > L).
@@ -333,6 +340,68 @@ void build_table(int type, int param, int L, int form, std::vector<float> &tf, s
     }
 }
 
+// Mantissa and exponent of a complex number: (re, im) = (mr, mi) 2^e with the
+// larger of |mr|, |mi| in [1/2, 1); zero gives (0, 0, 0).  The number is given
+// as 2^lg (cos ph, sin ph), so magnitudes far outside the FP64 range are fine.
+void split_exp(double lg, double ph, double &mr, double &mi, int &e) {
+    const double cr = std::cos(ph), ci = std::sin(ph);
+    const double mx = std::max(std::fabs(cr), std::fabs(ci));
+    const double l2 = lg + std::log2(mx);
+    e = (int)std::floor(l2) + 1;
+    const double s = std::exp2(l2 - e) / mx;
+    mr = cr * s;
+    mi = ci * s;
+}
+
+// Append the imaginary-node table of one (type, L, param) key: N = L + 1 or
+// L + 2, whichever is odd, nodes j = 0 .. (N - 1) / 2 of the conjugate-symmetric
+// half.  With w = e^{-2 pi i / N}: c_j = (m_j / N) sum_s v(s) w^{-j s} (the
+// stable form's coefficients, m_j = 1 for j = 0 and 2 otherwise), alpha_j =
+// (1 + w^j) / 2 = cos(pi j / N) e^{-i pi j / N}, t_j = tan(pi j / N),
+// C_j = c_j alpha_j^L (the kernels form D_j = i t_j C_j).  All in FP64 on the host; the
+// magnitude of alpha_j^L is carried as a base-2 logarithm, cos(pi j / N) taken
+// as sin(pi (N - 2j) / 2N) to keep its relative accuracy near j = N / 2.
+void build_table_im(int type, int param, int L, std::vector<float> &tf, std::vector<double> &td) {
+    const int N = (L % 2 == 0) ? L + 1 : L + 2;
+    const int J = (N - 1) / 2 + 1;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> cosk(N), sink(N);  // cos, sin of 2 pi k / N
+    for (int k = 0; k < N; ++k) {
+        cosk[k] = std::cos(2.0 * pi * (double)k / (double)N);
+        sink[k] = std::sin(2.0 * pi * (double)k / (double)N);
+    }
+    for (int j = 0; j < J; ++j) {
+        const double mult = j == 0 ? 1.0 : 2.0;
+        double cr = 0.0, ci = 0.0;
+        for (int s = 0; s <= L; ++s) {
+            const int k = (int)(((long long)j * s) % N);
+            const double v = (double)truth_value(type, param, s);
+            cr += v * cosk[k];
+            ci += v * sink[k];
+        }
+        cr *= mult / N;
+        ci *= mult / N;
+        const double sn = std::sin(pi * (double)j / (double)N);
+        const double cs = std::sin(pi * (double)(N - 2 * j) / (2.0 * (double)N));  // cos(pi j / N) > 0
+        const double t = sn / cs;
+        double Cr = 0.0, Ci = 0.0;
+        int ec = 0;
+        const double cabs = std::hypot(cr, ci);
+        if (cabs > 0.0) {
+            const double lg = std::log2(cabs) + (double)L * std::log2(cs);
+            const double ph = std::atan2(ci, cr) - pi * (double)(((long long)L * j) % (2LL * N)) / (double)N;
+            split_exp(lg, ph, Cr, Ci, ec);
+        }
+        int32_t eci = ec;
+        float fec;
+        std::memcpy(&fec, &eci, 4);
+        const float ft[4] = {(float)t, (float)Cr, (float)Ci, fec};
+        tf.insert(tf.end(), ft, ft + 4);
+        const double dt[4] = {t, Cr, Ci, (double)ec};
+        td.insert(td.end(), dt, dt + 4);
+    }
+}
+
 // Warp tasks for one node R: node tasks (longest first), then product tasks,
 // then clause tasks.  Segments are node constraints followed by product
 // constraints, each group sorted by length, descending.
@@ -355,7 +424,7 @@ int clause_groups_per_task(int groups, int other_tasks, int warps) {
 }
 
 void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clause, int n_xor2, int node_r,
-                 int warps, TaskSet &ts) {
+                 int warps, bool imag, TaskSet &ts) {
     ts.tasks.clear();
     ts.node_r = node_r;
     auto group = [&](int first, int count, int kind, int R) {
@@ -363,13 +432,13 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
         const int end = first + count;
         while (i < end) {
             const int L = seg_len[i];
-            const int nr = kind == TASK_NODE ? node_nr(L, R) : R;
+            const int nr = kind == TASK_NODE ? node_nr(L, R, imag) : R;
             const int G = seg_lanes(L, nr);
             const int S = 32 / G;
             int k = 0;
             while (k < S && i + k < end) {
                 const int Lk = seg_len[i + k];
-                const int nk = kind == TASK_NODE ? node_nr(Lk, R) : R;
+                const int nk = kind == TASK_NODE ? node_nr(Lk, R, imag) : R;
                 if (nk != nr || seg_lanes(Lk, nk) != G) break;
                 ++k;
             }
@@ -625,7 +694,7 @@ void build_image(ffsat_instance *I, int k) {
     for (size_t s = 0; s < I->seg_info.size(); ++s) {
         const int4 si = I->seg_info[s];
         const bool node = (int)s < I->n_node_seg;
-        const int R = node ? node_nr(si.y, nr) : kProdR;
+        const int R = node ? node_nr(si.y, nr, I->opt.form == FFSAT_FORM_STABLE) : kProdR;
         const int G = seg_lanes(si.y, R);
         const int32_t pad = node ? I->pad_node : I->n;
         const int32_t off = (int32_t)lits.size();
@@ -957,7 +1026,15 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     std::map<std::tuple<int, int, int>, int32_t> tab_index;
     std::vector<float> tab_f;
     std::vector<double> tab_d;
-    std::vector<int32_t> cons_tab(n_cons, -1);
+    // the imaginary-node tables serve the stable form's node tasks, the generic
+    // tables the paper form's and the plain FP64 comparator
+    const bool node_imag = opt.form == FFSAT_FORM_STABLE;
+    // entry 0 is an all-zero node (t = 0, C = D = 0): the node tasks read it past
+    // the end of a segment that is shorter than the longest one of its task
+    std::map<std::tuple<int, int, int>, int32_t> tab_im_index;
+    std::vector<float> tab_im_f(4, 0.0f);
+    std::vector<double> tab_im_d(4, 0.0);
+    std::vector<int32_t> cons_tab(n_cons, -1), seg_tab(n_cons, -1);
     int max_node_len = 0;
     for (int32_t c : node_c) {
         const int L = P->len[c];
@@ -971,6 +1048,16 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
             it = tab_index.emplace(key, off).first;
         }
         cons_tab[c] = it->second;
+        seg_tab[c] = it->second;
+        if (node_imag) {
+            auto jt = tab_im_index.find(key);
+            if (jt == tab_im_index.end()) {
+                const int32_t off = (int32_t)(tab_im_f.size() / 4);
+                build_table_im(t, p, L, tab_im_f, tab_im_d);
+                jt = tab_im_index.emplace(key, off).first;
+            }
+            seg_tab[c] = jt->second;
+        }
         max_node_len = std::max(max_node_len, L);
     }
 
@@ -983,13 +1070,13 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
         seg_len.push_back(P->len[c]);
         for (int64_t i = row_ptr[c]; i < row_ptr[c + 1]; ++i) seg_lits.push_back(pack_lit(lits[i]));
     };
-    for (int32_t c : node_c) add_seg(c, cons_tab[c]);
+    for (int32_t c : node_c) add_seg(c, seg_tab[c]);
     for (int32_t c : prod_c) {
         const int t = type[c];
         add_seg(c, t == FFSAT_OR ? PROD_OR : ((param[c] & 1) ? PROD_XOR_ODD : PROD_XOR_EVEN));
     }
     P->n_node_seg = (int)node_c.size();
-    P->pad_node = opt.form == FFSAT_FORM_PAPER ? n_vars + 1 : n_vars;
+    P->pad_node = n_vars + 1;  // x = 0: a factor of exactly 1 in both node forms
     P->seg_wd.assign(seg_len.size(), 0.0);
     // clauses of <= 3 literals: bank-ordered, then padded to whole tasks with
     // zero-weight clauses on the dummy variable
@@ -1049,8 +1136,8 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     P->nr[0] = nr32;
     P->nr[1] = nr64;
     TaskSet ts32, ts64;
-    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, nr32, fused_threads(false, nr32) / 32, ts32);
-    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, nr64, fused_threads(true, nr64) / 32, ts64);
+    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, nr32, fused_threads(false, nr32) / 32, node_imag, ts32);
+    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, nr64, fused_threads(true, nr64) / 32, node_imag, ts64);
     P->tasks[0] = ts32.tasks;
     P->tasks[1] = ts64.tasks;
     build_image(P, 0);
@@ -1059,7 +1146,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     const bool tune = opt.autotune && !node_c.empty() && opt.node_r == 0 && max_node_len <= 8 * 32;
     if (tune) {
         TaskSet ts8;
-        build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, 8, fused_threads(false, 8) / 32, ts8);
+        build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, 8, fused_threads(false, 8) / 32, node_imag, ts8);
         P->n_images = 3;
         P->nr[2] = 8;
         P->tasks[2] = ts8.tasks;
@@ -1089,6 +1176,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     P->off_clause_wd = A.put(P->clause_wd);
     P->off_seg_wd = A.put(P->seg_wd);
     const size_t o_tf = A.put(tab_f), o_td = A.put(tab_d);
+    const size_t o_tif = A.put(tab_im_f), o_tid = A.put(tab_im_d);
     const size_t o_rp = A.put(rp32), o_lits = A.put(lp32), o_type = A.put(P->type), o_par = A.put(par32);
     const size_t o_ctab = A.put(cons_tab);
     P->off_cons_wd = A.put(P->cons_wd);
@@ -1135,8 +1223,9 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     V.seg_wd = reinterpret_cast<const double *>(base + P->off_seg_wd);
     V.tab_f = reinterpret_cast<const float4 *>(base + o_tf);
     V.tab_d = reinterpret_cast<const double *>(base + o_td);
-    V.pad_y_f = opt.form == FFSAT_FORM_PAPER ? 0.0f : 1.0f;
-    V.pad_y_d = opt.form == FFSAT_FORM_PAPER ? 0.0 : 1.0;
+    V.tab_im_f = reinterpret_cast<const float4 *>(base + o_tif);
+    V.tab_im_d = reinterpret_cast<const double *>(base + o_tid);
+    V.node_form = node_imag ? NODE_FORM_IMAG : NODE_FORM_GENERIC;
     V.f_const = reinterpret_cast<const double *>(base + P->off_f_const);
     V.fix_s1 = P->fix_s1;
     V.fix_s2 = P->fix_s2;

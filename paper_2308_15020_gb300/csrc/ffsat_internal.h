@@ -35,6 +35,10 @@ enum : int32_t { PROD_OR = 0, PROD_XOR_EVEN = 1, PROD_XOR_ODD = 2 };
 // accumulator is then two int32 words per variable, see fix_s1).
 enum : int32_t { SMEM_FULL = 0, SMEM_X = 1, SMEM_NONE = 2, SMEM_RES = 3 };
 
+// Node task of an instance: the imaginary-node form (stable form) or the
+// generic alpha + beta y factors (paper form).
+enum : int32_t { NODE_FORM_IMAG = 0, NODE_FORM_GENERIC = 1 };
+
 // Device status bits.
 enum : int32_t { STATUS_NAN = 1, STATUS_OTHER = 2 };
 
@@ -61,12 +65,19 @@ struct DevView {
     // memory beside x and g, the kernel copies it there once per CTA.
     const int4 *res_image;
     int32_t res_int4, res_off_tasks, res_off_clauses, res_off_segmeta, res_off_lits, pad1;
-    // node tables, 8 reals per node: alpha.re, alpha.im, beta.re, beta.im, d.re, d.im, c.re, c.im
+    // node tables of the generic node task (paper form) and of the plain FP64
+    // comparator, 8 reals per node: alpha.re, alpha.im, beta.re, beta.im, d.re,
+    // d.im, c.re, c.im
     const float4 *tab_f;
     const double *tab_d;
-    float pad_y_f;   // literal value that makes a node factor exactly 1 (+1 stable form, 0 paper form)
-    float pad2;
-    double pad_y_d;
+    // node tables of the imaginary-node form (stable form), 4 words per node:
+    // FP32 {t, C.re, C.im, ec (int bits)}, FP64 {t, C.re, C.im, ec}; the C
+    // mantissa has its largest component in [1/2, 1) and is scaled by 2^ec;
+    // entry 0 is an all-zero node
+    const float4 *tab_im_f;
+    const double *tab_im_d;
+    int32_t node_form;  // NODE_FORM_IMAG or NODE_FORM_GENERIC: which node task runs
+    int32_t pad2;
     // device constants of f under the current weights: [0] = sum over clauses of
     // -w plus sum of w FE over constant constraints (fused kernel), [1] = the
     // latter alone (plain FP64 path); rewritten on the device by the ERWA update

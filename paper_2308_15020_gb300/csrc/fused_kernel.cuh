@@ -17,23 +17,24 @@
 //    all-but-one products formed by in-lane suffix/prefix products and a
 //    butterfly over the segment's lanes.
 //  * node: the DFT evaluation of Alg. 2 with conjugate symmetry.  For node j of
-//    N = L+1 roots of unity the factor of literal i is alpha_j + beta_j y_i
-//    (Eq. forward), the node value is the product over literals (Eq. reduction),
+//    N roots of unity the factor of literal i is alpha_j + beta_j y_i (Eq.
+//    forward), the node value is the product over literals (Eq. reduction),
 //    FE = Re sum_j c_j prod_i(.) (Eq. inverse with the preprocessed
 //    coefficients) and dFE/dy_i = Re sum_j d_j prod_{l != i}(.) (Eq. chain),
-//    d_j = c_j beta_j.  The all-but-one products come from in-lane suffix
-//    products, a butterfly over the segment lanes and an in-lane prefix pass;
-//    NI nodes are processed per iteration to give the scheduler independent
-//    multiply chains.
+//    d_j = c_j beta_j.  The stable form runs it as the paper's E(z) =
+//    prod (1 + y_i z) at the imaginary nodes z_j = i tan(pi j / N) with the
+//    per-node scale carried as an exponent (node_task_im); the paper form runs
+//    the generic factors (node_task).  The all-but-one products come from
+//    in-lane suffix products, a product over the segment lanes and an in-lane
+//    prefix pass.
 // Projected gradient descent (App. A.3 with a fixed step), the exact sign check
 // (Thm. "SAT Certificate", evaluated on integers) and the uniform restart of
 // Alg. 1 run in the same launch.
 //
 // Literals are packed as variable | (negated << 31).  Padding literals name two
 // dummy variables that follow the n real ones in shared memory: x[n] = +1 and
-// x[n+1] = 0, which make a clause, product or stable-form node factor (resp.
-// a paper-form node factor) exactly 1; their gradients land in dummy
-// accumulator slots.  When x or g live in global memory, accesses to the dummy
+// x[n+1] = 0, which make a clause or product factor (resp. a node factor of
+// either form) exactly 1; their gradients land in dummy accumulator slots.  When x or g live in global memory, accesses to the dummy
 // variables are resolved without touching memory.
 #pragma once
 
@@ -77,6 +78,58 @@ __device__ __forceinline__ Node<double> load_node(const DevView &V, double, int 
     const double2 p = __ldg(t), q = __ldg(t + 1), r = __ldg(t + 2), s = __ldg(t + 3);
     return {{p.x, p.y}, {q.x, q.y}, {r.x, r.y}, {s.x, s.y}};
 }
+
+// Node of the imaginary-node form: t = tan(pi j / N) and the coefficient
+// C_j = c_j alpha_j^L as a mantissa (largest component in [1/2, 1)) times 2^ec;
+// D_j = i t_j C_j is formed from them.
+template <typename R>
+struct NodeIm {
+    R t;
+    C2<R> c;
+    int ec;
+};
+
+__device__ __forceinline__ NodeIm<float> load_node_im(const DevView &V, float, int idx) {
+    const float4 p = __ldg(&V.tab_im_f[idx]);
+    return {p.x, {p.y, p.z}, __float_as_int(p.w)};
+}
+
+__device__ __forceinline__ NodeIm<double> load_node_im(const DevView &V, double, int idx) {
+    const double2 *t = reinterpret_cast<const double2 *>(V.tab_im_d) + 2 * idx;
+    const double2 p = __ldg(t), q = __ldg(t + 1);
+    return {p.x, {p.y, q.x}, (int)q.y};
+}
+
+// e such that max(|a|, |b|) 2^-e lies in [1/2, 1) (a, b finite, not both zero;
+// integer operations on the exponent field only).
+__device__ __forceinline__ int frexp_max(float a, float b) {
+    const int ia = __float_as_int(a) & 0x7fffffff, ib = __float_as_int(b) & 0x7fffffff;
+    return (max(ia, ib) >> 23) - 126;
+}
+__device__ __forceinline__ int frexp_max(double a, double b) {
+    const long long ia = __double_as_longlong(a) & 0x7fffffffffffffffll;
+    const long long ib = __double_as_longlong(b) & 0x7fffffffffffffffll;
+    return (int)(max(ia, ib) >> 52) - 1022;
+}
+// 2^k built from its exponent field; 0 below the normal range (such terms are
+// below 2^-126 of the result), clamped at the top (never reached).
+__device__ __forceinline__ float exp2i(float, int k) {
+    k = min(max(k, -127), 127);
+    return __int_as_float((k + 127) << 23);
+}
+__device__ __forceinline__ double exp2i(double, int k) {
+    k = min(max(k, -1023), 1023);
+    return __longlong_as_double((long long)(k + 1023) << 52);
+}
+// Bring the cache line of node table entry idx into L1 ahead of its use.
+__device__ __forceinline__ void prefetch_node_im(const DevView &V, float, int idx) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(V.tab_im_f + idx));
+}
+__device__ __forceinline__ void prefetch_node_im(const DevView &V, double, int idx) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(V.tab_im_d + 4 * idx));
+}
+__device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double recip(double a) { return __drcp_rn(a); }
 
 // Where the warp tasks read the constraint data from: global memory, or the
 // CTA's shared-memory copy of the resident image.
@@ -417,6 +470,226 @@ __device__ __forceinline__ void node_task(const DevView &V, const Src &S, int4 t
 }
 
 // ---------------------------------------------------------------------------
+// node path, imaginary-node form (the stable form's default)
+// ---------------------------------------------------------------------------
+// The stable node factor alpha_j + beta_j y equals alpha_j (1 + z_j y) with
+// z_j = beta_j / alpha_j = (1 - w^j) / (1 + w^j) = i t_j, t_j = tan(pi j / N):
+// the paper's E(z) = prod_i (1 + y_i z) (Eq. forward / Eq. reduction) at the
+// images of the roots of unity, with the per-node scale alpha_j^L folded into
+// the coefficients C_j = c_j alpha_j^L and D_j = i t_j C_j (Eq. inverse, Eq.
+// chain).  N is odd (L + 1 or L + 2), so no node sits at w^j = -1 and t_j is
+// finite.  Every factor 1 + i u (u = t_j y) has real part 1, so a complex
+// product by it is two FMAs instead of four, and its modulus is at least 1, so
+// the all-but-one product of the other lanes is the segment's product divided
+// by this lane's (a well-conditioned division).  Magnitudes are tracked as
+// integer exponents (the per-constraint log-magnitude scaling): each lane's
+// product is normalised before the cross-lane product, and the terms get their
+// scale back through exponent-field arithmetic.  Per (node, literal): u (1
+// FMUL), suffix product (2 FFMA), prefix product (2 FFMA), Re(pre suf) (2
+// FFMA).
+template <typename R, int NR>
+struct NodeImConst {
+    // a lane's product of NR factors stays below 2^120 (FP32) when
+    // t <= 2^(120/NR); above it the suffix product is renormalised once, in the
+    // middle of the lane (only for NR = 16 segments longer than 337 literals)
+    static constexpr bool kMaySplit = sizeof(R) == 4 && NR >= 16;
+    static constexpr float kSplitT = 181.0f;
+    // exponent offset of the prefix values (FP32): keeps them in the normal
+    // range when the suffix products are large; removed from the result
+    static constexpr int kOff = sizeof(R) == 4 ? 64 : 0;
+};
+
+// In-lane state of one segment lane: its NR literal values y, the suffix
+// products of the current node and the gradient sums over the nodes.  (Packed
+// f32x2 FFMA2/FMUL2 for u and the gradient sums were measured slower on the
+// cardinality workload: fewer instructions, but more FMA-pipe throttling.)
+template <typename R, int NR>
+struct LaneIm {
+    using K = NodeImConst<R, NR>;
+    static constexpr int M = NR / 2;
+    R y[NR], u[NR], gacc[NR];
+    C2<R> suf[NR];
+    __device__ __forceinline__ void set_y(int r, R v) { y[r] = v; }
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) gacc[r] = R(0);
+    }
+    __device__ __forceinline__ R grad(int r) const { return gacc[r]; }
+    // suffix products suf[r] = prod_{k > r} (1 + i u_k), u = t y; returns this
+    // lane's product (renormalised by 2^-emid in the middle when split)
+    __device__ __forceinline__ C2<R> suffix(R t, bool split, int &emid) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) u[r] = t * y[r];
+        suf[NR - 1] = {R(1), R(0)};
+#pragma unroll
+        for (int r = NR - 1; r >= 1; --r) {
+            suf[r - 1] = {fma(-suf[r].im, u[r], suf[r].re), fma(suf[r].re, u[r], suf[r].im)};
+            if (K::kMaySplit && r - 1 == M && split) {
+                emid = frexp_max(suf[M].re, suf[M].im);
+                const R s = exp2i(R(0), -emid);
+                suf[M].re *= s;
+                suf[M].im *= s;
+            }
+        }
+        return {fma(-suf[0].im, u[0], suf[0].re), fma(suf[0].re, u[0], suf[0].im)};
+    }
+    // gacc[r] += Re(pre_r suf[r]) with pre_r = pre prod_{k < r} (1 + i u_k)
+    __device__ __forceinline__ void prefix(C2<R> pre, bool split, int emid) {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            if (K::kMaySplit && r == M + 1 && split) {
+                const R s = exp2i(R(0), -emid);
+                pre.re *= s;
+                pre.im *= s;
+            }
+            gacc[r] = fma(pre.re, suf[r].re, gacc[r]);
+            gacc[r] = fma(-pre.im, suf[r].im, gacc[r]);
+            if (r + 1 < NR) pre = {fma(-pre.im, u[r], pre.re), fma(pre.re, u[r], pre.im)};
+        }
+    }
+};
+
+template <typename R, int NR, bool FULL, int XG, typename Acc>
+__device__ __forceinline__ void node_task_im(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
+                                             const Acc &acc, bool want_g, R &facc) {
+    using K = NodeImConst<R, NR>;
+    const int n = V.n;
+    const int G = (task.x >> 8) & 0xff;
+    const int seg = lane >> (__ffs(G) - 1);
+    const int sl = lane & (G - 1);
+    const int c = task.y + seg;
+    const bool valid = seg < task.z;
+    int L = 0, toff = 0;
+    const int32_t *lits = nullptr;
+    R w = R(0);
+    LaneIm<R, NR> ln;
+    if (valid) {
+        const int4 meta = S.segmeta[c];
+        L = meta.y;
+        toff = meta.z;
+        w = seg_weight<R>(V, meta, c);
+        lits = S.seg_lits + meta.x + sl * NR;
+        uint32_t lp[NR];
+        load_lits<NR>(lits, lp);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) ln.set_y(r, gather<R, XG>(xrow, lp[r], n));  // padding: y = 0, factor 1
+    } else {
+#pragma unroll
+        for (int r = 0; r < NR; ++r) ln.set_y(r, R(0));
+    }
+    // nodes j = 0 .. (N - 1) / 2 of this segment; past them (a shorter segment
+    // of the same task) the table's entry 0, an all-zero node, is read
+    const int Jc = valid ? (L + 1) / 2 + 1 : 0;
+    ln.clear();
+    // node 0: t = 0, every factor is 1; FE gets C_0, the gradient nothing
+    R fe = R(0);
+    if (valid) {
+        const NodeIm<R> n0 = load_node_im(V, R(0), toff);
+        fe = n0.c.re * exp2i(R(0), n0.ec);
+    }
+    const int J = task.w;
+    NodeIm<R> nd = load_node_im(V, R(0), 1 < Jc ? toff + 1 : 0);
+    for (int j = 1; j < J; ++j) {
+        const NodeIm<R> nx = load_node_im(V, R(0), j + 1 < Jc ? toff + j + 1 : 0);
+        // the table is read in order: fetch 256 bytes ahead into L1
+        constexpr int kAhead = 256 / (4 * (int)sizeof(R));
+        if (j + kAhead < Jc) prefetch_node_im(V, R(0), toff + j + kAhead);
+        const bool split = K::kMaySplit && nd.t > R(K::kSplitT);
+        int emid = 0;
+        C2<R> P = ln.suffix(nd.t, split, emid);
+        // this lane's product, normalised: P 2^eown
+        const int e0 = frexp_max(P.re, P.im);
+        {
+            const R s = exp2i(R(0), -e0);
+            P.re *= s;
+            P.im *= s;
+        }
+        const int eown = e0 + emid;
+        // product over the segment's lanes: A 2^EA.  A full warp (FULL: G = 32)
+        // runs the five butterfly levels unconditionally and sums the exponents
+        // with one warp reduction; narrower segments take the levels below G
+        // (G is the same for the whole warp)
+        C2<R> A = P;
+        int EA;
+        if constexpr (FULL) {
+#pragma unroll
+            for (int s = 1; s < 32; s <<= 1) {
+                const C2<R> Ap = {__shfl_xor_sync(kFull, A.re, s), __shfl_xor_sync(kFull, A.im, s)};
+                A = cmul(A, Ap);
+            }
+            EA = __reduce_add_sync(kFull, eown);
+        } else {
+            EA = eown;
+#pragma unroll
+            for (int s = 1; s < 32; s <<= 1) {
+                if (s < G) {
+                    const C2<R> Ap = {__shfl_xor_sync(kFull, A.re, s), __shfl_xor_sync(kFull, A.im, s)};
+                    EA += __shfl_xor_sync(kFull, EA, s);
+                    A = cmul(A, Ap);
+                }
+            }
+        }
+        fe = fma(fma(nd.c.re, A.re, -nd.c.im * A.im), exp2i(R(0), nd.ec + EA), fe);  // Re(C_j Q_j)
+        // product of the other lanes X = A / P = A conj(P) / |P|^2 (|P| >= 1/2);
+        // pre = D_j X, scaled by 2^kOff (and by 2^emid while it meets
+        // renormalised suffix products)
+        const R sc = recip(fma(P.re, P.re, P.im * P.im)) * exp2i(R(0), nd.ec + EA - eown + K::kOff + emid);
+        const C2<R> AP = {fma(A.re, P.re, A.im * P.im), fma(A.im, P.re, -A.re * P.im)};
+        const C2<R> D = {-nd.t * nd.c.im, nd.t * nd.c.re};  // D_j = i t_j C_j
+        C2<R> pre = cmul(D, AP);
+        pre.re *= sc;
+        pre.im *= sc;
+        ln.prefix(pre, split, emid);
+        nd = nx;
+    }
+    if (valid && sl == 0) facc += w * fe;
+    if (want_g && valid) {
+        const R wg = w * exp2i(R(0), -K::kOff);
+        uint32_t lp[NR];
+        load_lits<NR>(lits, lp);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) scatter<R>(acc, lp[r], wg * ln.grad(r), n);
+    }
+}
+
+// A node task of either form, nr literals per lane (task bits 16..23): a kernel
+// built for NR = 16 also runs 12 and 8, one built for NR = 8 runs 8.
+template <typename R, int NR, int NI, bool SF, int XG, typename Acc>
+__device__ __forceinline__ void node_dispatch(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
+                                              const Acc &acc, bool want_g, R &facc) {
+    const int nr = (task.x >> 16) & 0xff;
+    if (V.node_form == NODE_FORM_IMAG) {
+        const bool full = ((task.x >> 8) & 0xff) == 32;
+        if constexpr (NR >= 16) {
+            if (nr == 12) {
+                if (full) node_task_im<R, 12, true, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+                else node_task_im<R, 12, false, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+            } else if (nr == 8) {
+                if (full) node_task_im<R, 8, true, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+                else node_task_im<R, 8, false, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+            } else {
+                if (full) node_task_im<R, 16, true, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+                else node_task_im<R, 16, false, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+            }
+        } else if constexpr (NR > 0) {
+            if (full) node_task_im<R, NR, true, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+            else node_task_im<R, NR, false, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+        }
+    } else {
+        if constexpr (NR >= 16) {
+            if (nr == 12)
+                node_task<R, 12, NI, SF, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+            else if (nr == 8)
+                node_task<R, 8, NI, SF, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+            else
+                node_task<R, 16, NI, SF, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+        } else if constexpr (NR > 0) {
+            node_task<R, NR, NI, SF, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // block helpers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
@@ -556,19 +829,9 @@ __device__ __forceinline__ R eval_tasks(const DevView &V, const Src &S, const R 
         } else if (kind == TASK_PROD) {
             prod_task<R, XG>(V, S, task, lane, xrow, G, want_g, facc);
         } else {
-            // node tasks carry their literals per lane in bits 16..23
-            const int nr = (task.x >> 16) & 0xff;
-            if constexpr (NR >= 16) {
-                // the batch kernel also meets images built with 8 literals per lane
-                if (nr == 12)
-                    node_task<R, 12, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
-                else if (nr == 8)
-                    node_task<R, 8, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
-                else
-                    node_task<R, 16, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
-            } else if constexpr (NR > 0) {
-                node_task<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
-            }
+            // node tasks carry their literals per lane in bits 16..23 (the batch
+            // kernel also meets images built with 8 literals per lane)
+            node_dispatch<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
         }
     }
     __syncthreads();
