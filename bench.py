@@ -53,11 +53,8 @@ WORKLOADS = {
 # milliseconds, so that the clock sampler sees it several times
 DEFAULT_STEPS = {"cnf_xor_n2000": 100, "3sat_n100": 200, "cnf_card_n20000": 10, "uneven_batch": 3}
 
-FP32_LANES_PER_SM = 128
 # shared memory: 32 banks x 4 bytes per clock per SM
 SMEM_BYTES_PER_CLK_SM = 128
-# FP64 arithmetic rate of the part (nominal; far below its FP32 rate)
-FP64_NOMINAL_TFLOPS = 1.25
 # algorithmic FP32 flops of the node path per (node, literal): factor (2 FMA = 4),
 # suffix product (complex multiply, 6), prefix product (6), Re(pre * suf) (3)
 NODE_FLOPS = 19
@@ -167,11 +164,17 @@ class ClockSampler:
 
     def mark(self):
         """Only samples taken after this call count (the timed region)."""
-        self.fh.flush()
+        if self.proc is not None:
+            self.fh.flush()
         self.t_mark = time.time()
+
+    def mark_end(self):
+        """End of the timed region: later samples (other measurements) do not count for it."""
+        self.t_end = time.time()
 
     def start(self):
         self.t_mark = 0.0
+        self.t_end = None
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
         try:
             self.fh = open(self.path, "w")
@@ -182,6 +185,7 @@ class ClockSampler:
             self.proc = None
 
     def stop(self):
+        """Stop sampling; clock statistics of the timed region [mark, mark_end]."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -190,6 +194,15 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.fh.close()
+        self.stopped = True
+        return self.window(self.t_mark, getattr(self, "t_end", None))
+
+    def window(self, t0, t1=None):
+        """Clock statistics of the samples taken in [t0, t1] (t1 None: to the end)."""
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        if not getattr(self, "stopped", False):
+            self.fh.flush()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         import datetime
@@ -201,8 +214,8 @@ class ClockSampler:
             try:
                 ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
             except ValueError:
-                ts = self.t_mark
-            if ts < self.t_mark - 0.05:
+                ts = t0
+            if ts < t0 - 0.05 or (t1 is not None and ts > t1 + 0.05):
                 continue
             try:
                 sm.append(float(parts[2]))
@@ -351,6 +364,7 @@ def fp32_vs_plain64(h, x, B: int, nnz: int, flush, stream):
     g32 = torch.empty_like(x32)
     g64 = torch.empty_like(x64)
     ms32 = time_evals(lambda: h.eval_grad(x32, f, g32, stream=stream), flush, 10, stream)
+    ms64f = time_evals(lambda: h.eval_grad(x64, f, g64, stream=stream), flush, 5, stream)
     one = time_evals(lambda: h.eval_grad_plain64(x64, f, g64, stream=stream), flush, 1, stream)
     ms64 = time_evals(lambda: h.eval_grad_plain64(x64, f, g64, stream=stream), flush, 3 if one < 500 else 1, stream)
     h.sync_status()
@@ -363,12 +377,137 @@ def fp32_vs_plain64(h, x, B: int, nnz: int, flush, stream):
     torch.cuda.synchronize()
     df = (f32 - f64).abs().max().item()
     dg = (g32.double() - g64).abs().max().item()
-    r32, r64 = B * nnz / (ms32 / 1e3), B * nnz / (ms64 / 1e3)
+    r32, r64, r64f = B * nnz / (ms32 / 1e3), B * nnz / (ms64 / 1e3), B * nnz / (ms64f / 1e3)
     return {"fp32_fused_eval": r32, "plain_fp64_gpu_eval": r64, "speedup": r32 / r64, "unit": UNIT,
             "fp32_eval_ms": ms32, "plain_fp64_eval_ms": ms64,
+            "fp64_fused_eval": r64f, "fp64_fused_eval_ms": ms64f, "speedup_fp32_over_fp64_fused": r32 / r64f,
             "fp32_error_vs_fp64": {"max_abs_f": df, "max_abs_f_over_max_abs_f64": df / max(f64.abs().max().item(), 1e-300),
                                    "max_abs_g": dg, "max_abs_g_over_max_abs_g64": dg / max(g64.abs().max().item(), 1e-300),
                                    "points": B}}
+
+
+def measure_alu_peaks(clocks, target_ms: float = 200.0):
+    """FMA throughput of this GPU in FP32 and FP64, measured by the library's
+    peak kernel (independent FMA chains on every SM, CUDA events), with the
+    median SM clock sampled during each measurement."""
+    from paper_2308_15020_gb300 import ffsat
+
+    out = {}
+    for name, dt in (("f32", ffsat.FFSAT_F32), ("f64", ffsat.FFSAT_F64)):
+        t0 = time.time()
+        tf, ms = ffsat.alu_peak(dt, target_ms=target_ms)
+        t1 = time.time()
+        clk = clocks.window(t0, t1) if clocks else {"sm_mhz": None, "reasons": None}
+        out[name] = {"tflops": tf, "launch_ms": ms, "sm_mhz": clk["sm_mhz"], "reasons": clk["reasons"]}
+    return out
+
+
+def alu_peak_source(alu, name: str) -> str:
+    a = alu[name]
+    clk = f", median SM clock {a['sm_mhz']:.0f} MHz" if a.get("sm_mhz") else ""
+    return (f"measured in this run: {name.upper()} FMA chains on every SM (ffsat_alu_peak, "
+            f"{a['launch_ms']:.0f} ms launch{clk})")
+
+
+def sec8d_hbm_bytes(st, B: int, T: int, elem: int) -> float:
+    """HBM bytes of T evaluations by the survey's per-evaluation model: read x
+    and write g (2 B n elem) plus f (8 B)."""
+    return T * (2.0 * B * st["n"] * elem + 8.0 * B)
+
+
+def node_path_record(args, alu, flush, stream, clocks, rank: int):
+    """The DFT (node) path on its own workload: CNF + at-least-K, n = 20000,
+    84000 3-clauses + 500 at-least-K constraints of length 64..512, B = 1024
+    points, FP32, T = 4 iterations per step; timed like the main line, with the
+    algorithmic FP32 flops of the node products against the measured FP32 peak,
+    and the FP32 result checked against the FP64 oracle on sampled points."""
+    import torch
+
+    from paper_2308_15020_gb300 import ffsat
+
+    build, B, _, T, lr = WORKLOADS["cnf_card_n20000"]
+    inst = build(0)
+    st = instance_stats(inst)
+    h = ffsat.Instance(inst)
+    x0 = torch.from_numpy(gen.uniform_points(B, inst.n, 1000 + rank)).cuda()
+    x = x0.clone()
+    solved = torch.empty(B, dtype=torch.uint8, device="cuda")
+    nun = torch.empty(B, dtype=torch.int32, device="cuda")
+    epoch = [0]
+
+    def one_step():
+        h.step(x, T=T, lr=lr, seed=7, epoch=epoch[0], b_offset=rank * B, restart=True, solved=solved, n_unsat=nun,
+               stream=stream)
+        epoch[0] += 1
+
+    for _ in range(3):
+        flush.zero_()
+        one_step()
+    torch.cuda.synchronize()
+    h.sync_status()
+    steps = args.node_path_steps
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    t0 = time.time()
+    for s_, e_ in evs:
+        flush.zero_()
+        s_.record(stream)
+        one_step()
+        e_.record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    h.sync_status()
+    total_ms = sum(s_.elapsed_time(e_) for s_, e_ in evs)
+    launch_s = total_ms / steps / 1e3
+    flops, _, _, _ = algorithmic_work(st, B, T, 4)
+    achieved = flops / launch_s / 1e12
+    peak = alu["f32"]["tflops"]
+    rec = {
+        "workload": "cnf_card_n20000", "B": B, "n": inst.n, "m": inst.m, "nnz": inst.nnz, "pgd_iters_per_step": T,
+        "lr": lr, "dtype": "f32", "form": "stable (imaginary nodes)", "steps": steps, "warmup": 3,
+        "ms_per_step": total_ms / steps, "value": B * inst.nnz * T * steps / (total_ms / 1e3), "unit": UNIT,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": alu_peak_source(alu, "f32"),
+                     "algorithmic_per_launch": flops,
+                     "flop_model": f"{NODE_FLOPS} FP32 flops per (node, literal) over floor((L+1)/2)+1 nodes per "
+                                   f"at-least-K constraint, {CLOSED_FLOPS} per closed-form literal",
+                     "traffic": profile_traffic("ffsat_fused", "cnf_card_n20000"),
+                     "ncu": profile_counters("ffsat_fused", "cnf_card_n20000")},
+        "clocks": clocks.window(t0, t1) if clocks else None,
+    }
+    if not args.no_cpu_baseline:
+        rec["cpu_baseline"] = node_path_oracle_leg(inst, h, x0, args.node_path_points)
+    return rec
+
+
+def node_path_oracle_leg(inst, h, x0, k: int):
+    """The FP64 oracle's evaluation of F and grad F at k of the points (all host
+    threads), timed, and the FP32 kernel's f and g at the same points compared
+    with it: normalised errors against the 1e-4 condition-scale tolerance (<= 1
+    is within it) and plain relative errors."""
+    import torch
+
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle as O
+
+    xk = x0[:k].contiguous()
+    f32, g32 = h.eval_grad(xk)
+    torch.cuda.synchronize()
+    f32, g32 = f32.cpu().numpy(), g32.cpu().numpy().astype(np.float64)
+    x64 = xk.cpu().numpy().astype(np.float64)
+    t0 = time.perf_counter()
+    fs, gs = O.eval_grad(inst, x64)
+    dt = time.perf_counter() - t0
+    sf, A = O.eval_scale(inst, x64, 1e-2)
+    ef = float(np.max(np.abs(f32 - fs) / (1e-4 * np.maximum(np.abs(fs), sf))))
+    eg = float(np.max(np.abs(g32 - gs) / (1e-4 * np.maximum(np.abs(gs), A))))
+    return {"value": k * inst.nnz / dt, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"one evaluation of F and grad F at {k} of the points, FP64 oracle, {dt:.2f} s",
+            "cpu_model": host_cpu_model(),
+            "fp32_error_vs_oracle": {
+                "points": k, "max_normalised_f": ef, "max_normalised_g": eg, "within_tolerance": ef <= 1 and eg <= 1,
+                "tolerance": "1e-4 x max(|exact|, condition scale); at-least-K literals floor 1e-2",
+                "max_abs_f_over_max_abs_f": float(np.max(np.abs(f32 - fs)) / max(np.max(np.abs(fs)), 1e-300)),
+                "max_abs_g_over_max_abs_g": float(np.max(np.abs(g32 - gs)) / max(np.max(np.abs(gs)), 1e-300))}}
 
 
 def run_reference(args, rank: int, world: int):
@@ -919,7 +1058,8 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clk = clocks.stop() if clocks else None
+    if clocks:
+        clocks.mark_end()
     h.sync_status()
     per = [s.elapsed_time(e) for s, e in evs]
     total_ms = sum(per)
@@ -930,9 +1070,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     work = B * inst.nnz * T
     value = world * work * args.steps / (total_ms / 1e3)
 
-    # ---- end-to-end through host buffers ----
+    # ---- end-to-end through host buffers: the points in, the points (the
+    # CLS's result), the solved flags and the violation counts out ----
     solved_h = torch.empty(B, dtype=torch.uint8).pin_memory()
     nun_h = torch.empty(B, dtype=torch.int32).pin_memory()
+    x_out_h = torch.empty_like(x_host).pin_memory()
     e2e_ms = []
     for i in range(args.steps):
         flush.zero_()
@@ -940,6 +1082,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         t0 = time.perf_counter()
         x.copy_(x_host, non_blocking=True)
         one_step()
+        x_out_h.copy_(x, non_blocking=True)
         solved_h.copy_(solved, non_blocking=True)
         nun_h.copy_(nun, non_blocking=True)
         torch.cuda.synchronize()
@@ -951,12 +1094,19 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         e2e_total = float(t.item())
     e2e_value = world * work * args.steps / (e2e_total / 1e3)
     h2d = B * inst.n * x_host.element_size()
-    d2h = B * (solved_h.element_size() + nun_h.element_size())
+    d2h = B * inst.n * x_out_h.element_size() + B * (solved_h.element_size() + nun_h.element_size())
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
+
+    # ---- measured FMA peaks (the arithmetic roofline denominators) and the
+    # node (DFT) path's own record; the clock sampler is still running ----
+    alu = measure_alu_peaks(clocks)
+    node_rec = None
+    if args.workload == "cnf_xor_n2000" and world == 1 and not args.no_node_path:
+        node_rec = node_path_record(args, alu, flush, stream, clocks, rank)
 
     # ---- roofline of the fused step kernel (the only kernel of a step) ----
     peaks, peak_src = load_peaks()
@@ -965,38 +1115,45 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
     resident = h.info()["smem_mode_f64" if dtname == "f64" else "smem_mode_f32"] in (0, 3)
+    elem = 8 if dtname == "f64" else 4
+    hbm_8d = sec8d_hbm_bytes(st, B, T, elem)
     if dtname == "f64":
-        # the FP64 pipe: GB300 executes FP64 at a small fraction of its FP32 rate;
-        # no measured FP64 peak exists, so the part's nominal 1.25 TFLOP/s is the peak
-        peak = FP64_NOMINAL_TFLOPS
+        # the FP64 pipe: GB300 executes FP64 at a small fraction of its FP32 rate
+        peak = alu["f64"]["tflops"]
         achieved = flops / launch_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": "nominal FP64 rate of the part (no measured FP64 peak; fallback)",
-                "algorithmic_per_launch": flops,
+                "peak_source": alu_peak_source(alu, "f64"), "algorithmic_per_launch": flops,
                 "smem": {"achieved": smem_bytes / launch_s / 1e9,
                          "peak": n_sm * SMEM_BYTES_PER_CLK_SM * sm_max * 1e6 / 1e9, "unit": "GB/s"}}
     elif not alu_bound and resident:
-        # x and the gradient stay in shared memory for all T iterations: the gathers
-        # and scatter-adds through the shared-memory pipe bound the step
-        peak = n_sm * SMEM_BYTES_PER_CLK_SM * sm_max * 1e6 / 1e9
-        achieved = smem_bytes / launch_s / 1e9
-        roof = {"bound": "smem", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{n_sm} SMs x 128 B/clk shared memory x {sm_max:.0f} MHz (max SM clock, "
-                               f"{peak_src} peaks file)",
-                "algorithmic_per_launch": smem_bytes,
-                "hbm": {"achieved": bytes_ / launch_s / 1e9, "peak": float(peaks["hbm_gbs"]),
-                        "algorithmic_per_launch": bytes_}}
+        # the survey's model of this workload: memory/gather-bound, 2 B n 4 + 8 B
+        # bytes per evaluation; x and the gradient stay in shared memory for all T
+        # iterations here, so the on-chip shared-memory pipe is the bound that the
+        # kernel actually meets (reported beside it)
+        peak = float(peaks["hbm_gbs"])
+        achieved = hbm_8d / launch_s / 1e9
+        smem_peak = n_sm * SMEM_BYTES_PER_CLK_SM * sm_max * 1e6 / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "peak_source": f"{peak_src} HBM copy bandwidth (MEASURED_PEAKS.json)",
+                "algorithmic_per_launch": hbm_8d,
+                "model": "T x (2 B n x 4 bytes of x and g + 8 B bytes of f) per launch",
+                "on_chip": {"bound": "smem", "achieved": smem_bytes / launch_s / 1e9, "peak": smem_peak,
+                            "unit": "GB/s", "frac": smem_bytes / launch_s / 1e9 / smem_peak,
+                            "algorithmic_per_launch": smem_bytes,
+                            "model": "one x read and one gradient update (4 bytes each) per closed-form literal "
+                                     "per point per iteration",
+                            "peak_source": f"{n_sm} SMs x 128 B/clk x {sm_max:.0f} MHz"},
+                "dram_per_launch_once": bytes_}
     elif alu_bound:
-        peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        peak = alu["f32"]["tflops"]
         achieved = flops / launch_s / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": f"FP32 FMA lanes x 2 x {sm_max:.0f} MHz (max SM clock, {peak_src} peaks file)",
-                "algorithmic_per_launch": flops}
+                "peak_source": alu_peak_source(alu, "f32"), "algorithmic_per_launch": flops}
     else:
         peak = float(peaks["hbm_gbs"])
-        achieved = bytes_ / launch_s / 1e9
+        achieved = hbm_8d / launch_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_per_launch": bytes_}
+                "peak_source": f"{peak_src} HBM copy bandwidth", "algorithmic_per_launch": hbm_8d}
     prof_kernel = "ffsat_cluster" if ctas_per_point > 1 else "ffsat_fused"
     roof["traffic"] = profile_traffic(prof_kernel, args.workload)
     roof["ncu"] = profile_counters(prof_kernel, args.workload)
@@ -1005,6 +1162,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(inst, B, T, lr, target_s=args.cpu_seconds)
     vs64 = fp32_vs_plain64(h, x0, B, inst.nnz, flush, stream) if not args.no_plain64 else None
+    clk = clocks.stop() if clocks else None
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -1020,8 +1178,11 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clk,
+        "alu_peaks_measured": alu,
         "kernel_source_hash": kernel_source_hash("cluster" if ctas_per_point > 1 else "fused"),
     }
+    if node_rec is not None:
+        line["node_path"] = node_rec
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -1094,7 +1255,8 @@ def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clk = clocks.stop() if clocks else None
+    if clocks:
+        clocks.mark_end()
     total_ms = sum(s.elapsed_time(e) for s, e in evs)
     if dist:
         t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
@@ -1126,24 +1288,22 @@ def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
         if dist:
             dist.destroy_process_group()
         return
-    peaks, peak_src = load_peaks()
     flops = bytes_ = 0.0
     for i in insts:
         fl, by, _, _ = algorithmic_work(instance_stats(i), B, T)
         flops += fl
         bytes_ += by
     launch_s = (total_ms / args.steps) / 1e3
-    n_sm = torch.cuda.get_device_properties(local_rank).multi_processor_count
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    alu = measure_alu_peaks(clocks)
+    peak = alu["f32"]["tflops"]
     roof = {"bound": "alu", "achieved": flops / launch_s / 1e12, "peak": peak, "unit": "TFLOP/s",
-            "frac": flops / launch_s / 1e12 / peak,
-            "peak_source": f"FP32 FMA lanes x 2 x {sm_max:.0f} MHz (max SM clock, {peak_src} peaks file)",
+            "frac": flops / launch_s / 1e12 / peak, "peak_source": alu_peak_source(alu, "f32"),
             "algorithmic_per_launch": flops, "traffic": profile_traffic("ffsat_batch", args.workload),
             "ncu": profile_counters("ffsat_batch", args.workload)}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline_batch(insts, B, T, lr, target_s=args.cpu_seconds)
+    clk = clocks.stop() if clocks else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1157,7 +1317,8 @@ def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
         "e2e": {"value": world * work * args.steps / (e2e_total / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(sum(x.numel() * x.element_size() for x in xs_host)),
                 "d2h_bytes_per_step": int(B * len(insts))},
-        "gpu_launches": launches_per_step * args.steps, "clocks": clk, "kernel_source_hash": kernel_source_hash(),
+        "gpu_launches": launches_per_step * args.steps, "clocks": clk, "alu_peaks_measured": alu,
+        "kernel_source_hash": kernel_source_hash(),
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -1183,6 +1344,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-node-path", action="store_true",
+                    help="default line: skip the DFT node-path record (CNF + at-least-K n=20000)")
+    ap.add_argument("--node-path-steps", type=int, default=5, help="timed steps of the node-path record")
+    ap.add_argument("--node-path-points", type=int, default=4,
+                    help="points of the node-path record checked against the FP64 oracle")
     ap.add_argument("--no-plain64", action="store_true",
                     help="skip the FP32-fused vs plain-FP64-GPU single-evaluation comparison")
     args = ap.parse_args()

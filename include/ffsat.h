@@ -398,6 +398,18 @@ int32_t ffsat_last_launch_count(void);
  * thread (1 unless it ran one thread-block cluster per point; 0 before any). */
 int32_t ffsat_last_cluster_size(void);
 
+/* Measured fused multiply-add throughput of the current device, for the
+ * arithmetic rooflines of a benchmark (the paper has no counterpart).
+ * dtype FFSAT_F32 or FFSAT_F64.  Runs independent FMA chains on every SM
+ * (4 CTAs of 256 threads per SM, 8 chains per thread) in one launch sized to
+ * take about target_ms milliseconds (0 < target_ms <= 10000) after a warm-up
+ * launch, timed with CUDA events on `stream`, and writes the rate in TFLOP/s
+ * (2 flops per FMA) to *tflops and the timed launch's duration to *ms (may be
+ * NULL).  Synchronous: it waits for its launches.  Allocates and frees a small
+ * output buffer; reads and changes no clock setting.  Returns FFSAT_ERR_ARG for
+ * a bad dtype / target or NULL tflops, FFSAT_ERR_CUDA if a launch fails. */
+int ffsat_alu_peak(int32_t dtype, double target_ms, double *tflops, double *ms, void *stream);
+
 /* Message for the last error on this thread ("" if none). */
 const char *ffsat_last_error(void);
 

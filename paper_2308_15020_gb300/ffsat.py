@@ -71,6 +71,7 @@ SYMBOLS = (
     "ffsat_instance_info",
     "ffsat_last_launch_count",
     "ffsat_last_cluster_size",
+    "ffsat_alu_peak",
     "ffsat_last_error",
     "ffsat_free",
 )
@@ -211,6 +212,8 @@ def lib():
         L.ffsat_restart_from_proposal.argtypes = [_vp, C.c_int32, _vp, C.c_int32, _vp, C.c_float, _vp, C.c_uint64,
                                                   C.c_uint64, C.c_uint64, _vp]
         L.ffsat_restart_from_proposal.restype = C.c_int
+        L.ffsat_alu_peak.argtypes = [C.c_int32, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double), _vp]
+        L.ffsat_alu_peak.restype = C.c_int
         L.ffsat_mpnn_free.argtypes = [_vp]
         L.ffsat_mpnn_free.restype = None
         L.ffsat_sync_status.argtypes = [_vp, _vp]
@@ -241,6 +244,14 @@ def last_launch_count() -> int:
 def last_cluster_size() -> int:
     """CTAs per point of the last step call on this thread (1: one CTA per point)."""
     return int(lib().ffsat_last_cluster_size())
+
+
+def alu_peak(dtype: int = FFSAT_F32, target_ms: float = 50.0, stream=None):
+    """Measured FMA throughput of the current device (TFLOP/s) and the timed
+    launch's duration (ms): FFSAT_F32 or FFSAT_F64."""
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().ffsat_alu_peak(int(dtype), float(target_ms), C.byref(tf), C.byref(ms), _stream(stream)))
+    return tf.value, ms.value
 
 
 def _ptr(t) -> Optional[int]:

@@ -98,3 +98,7 @@ def test_clock_parser_keeps_the_timed_region(bench, tmp_path):
     assert out["samples"] == 2 and out["sm_mhz"] == pytest.approx(2062.5) and out["sm_max_mhz"] == 2070.0
     assert out["reasons"] == ["sw_power_cap"]
     assert np.isfinite(out["sm_mhz"])
+    # a window that ends before the last sample (the end of the timed region)
+    t1 = datetime.datetime.strptime("2026/01/01 00:00:01.000", "%Y/%m/%d %H:%M:%S.%f").timestamp()
+    w = s.window(t1 - 0.01, t1 - 0.01)  # samples within 50 ms of the window count
+    assert w["samples"] == 1 and w["sm_mhz"] == 2070.0 and w["reasons"] == []
