@@ -112,7 +112,8 @@ __device__ __forceinline__ int frexp_max(double a, double b) {
     return (int)(max(ia, ib) >> 52) - 1022;
 }
 // 2^k built from its exponent field; 0 below the normal range (such terms are
-// below 2^-126 of the result), clamped at the top (never reached).
+// below 2^-126 of the result), clamped at the top (reached only when the
+// coefficient it scales is zero).
 __device__ __forceinline__ float exp2i(float, int k) {
     k = min(max(k, -127), 127);
     return __int_as_float((k + 127) << 23);
@@ -120,6 +121,17 @@ __device__ __forceinline__ float exp2i(float, int k) {
 __device__ __forceinline__ double exp2i(double, int k) {
     k = min(max(k, -1023), 1023);
     return __longlong_as_double((long long)(k + 1023) << 52);
+}
+// s = 2^-e with e = frexp_max(a, b), built from the exponent field of the larger
+// of |a|, |b| (a, b finite, the larger normal and below 2^126).
+__device__ __forceinline__ float norm_scale(float a, float b, int &e) {
+    const int m = max(__float_as_int(a) & 0x7fffffff, __float_as_int(b) & 0x7fffffff) & 0x7f800000;
+    e = (m >> 23) - 126;
+    return __int_as_float(0x7e800000 - m);
+}
+__device__ __forceinline__ double norm_scale(double a, double b, int &e) {
+    e = frexp_max(a, b);
+    return exp2i(0.0, -e);
 }
 // Bring the cache line of node table entry idx into L1 ahead of its use.
 __device__ __forceinline__ void prefetch_node_im(const DevView &V, float, int idx) {
@@ -551,7 +563,7 @@ struct LaneIm {
 
 template <typename R, int NR, bool FULL, int XG, typename Acc>
 __device__ __forceinline__ void node_task_im(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
-                                             const Acc &acc, bool want_g, R &facc) {
+                                             const Acc &acc, bool want_g, R &facc, bool want_f) {
     using K = NodeImConst<R, NR>;
     const int n = V.n;
     const int G = (task.x >> 8) & 0xff;
@@ -598,9 +610,9 @@ __device__ __forceinline__ void node_task_im(const DevView &V, const Src &S, int
         int emid = 0;
         C2<R> P = ln.suffix(nd.t, split, emid);
         // this lane's product, normalised: P 2^eown
-        const int e0 = frexp_max(P.re, P.im);
+        int e0;
         {
-            const R s = exp2i(R(0), -e0);
+            const R s = norm_scale(P.re, P.im, e0);
             P.re *= s;
             P.im *= s;
         }
@@ -629,7 +641,7 @@ __device__ __forceinline__ void node_task_im(const DevView &V, const Src &S, int
                 }
             }
         }
-        fe = fma(fma(nd.c.re, A.re, -nd.c.im * A.im), exp2i(R(0), nd.ec + EA), fe);  // Re(C_j Q_j)
+        if (want_f) fe = fma(fma(nd.c.re, A.re, -nd.c.im * A.im), exp2i(R(0), nd.ec + EA), fe);  // Re(C_j Q_j)
         // product of the other lanes X = A / P = A conj(P) / |P|^2 (|P| >= 1/2);
         // pre = D_j X, scaled by 2^kOff (and by 2^emid while it meets
         // renormalised suffix products)
@@ -656,24 +668,24 @@ __device__ __forceinline__ void node_task_im(const DevView &V, const Src &S, int
 // built for NR = 16 also runs 12 and 8, one built for NR = 8 runs 8.
 template <typename R, int NR, int NI, bool SF, int XG, typename Acc>
 __device__ __forceinline__ void node_dispatch(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
-                                              const Acc &acc, bool want_g, R &facc) {
+                                              const Acc &acc, bool want_g, R &facc, bool want_f = true) {
     const int nr = (task.x >> 16) & 0xff;
     if (V.node_form == NODE_FORM_IMAG) {
         const bool full = ((task.x >> 8) & 0xff) == 32;
         if constexpr (NR >= 16) {
             if (nr == 12) {
-                if (full) node_task_im<R, 12, true, XG>(V, S, task, lane, xrow, acc, want_g, facc);
-                else node_task_im<R, 12, false, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+                if (full) node_task_im<R, 12, true, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
+                else node_task_im<R, 12, false, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
             } else if (nr == 8) {
-                if (full) node_task_im<R, 8, true, XG>(V, S, task, lane, xrow, acc, want_g, facc);
-                else node_task_im<R, 8, false, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+                if (full) node_task_im<R, 8, true, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
+                else node_task_im<R, 8, false, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
             } else {
-                if (full) node_task_im<R, 16, true, XG>(V, S, task, lane, xrow, acc, want_g, facc);
-                else node_task_im<R, 16, false, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+                if (full) node_task_im<R, 16, true, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
+                else node_task_im<R, 16, false, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
             }
         } else if constexpr (NR > 0) {
-            if (full) node_task_im<R, NR, true, XG>(V, S, task, lane, xrow, acc, want_g, facc);
-            else node_task_im<R, NR, false, XG>(V, S, task, lane, xrow, acc, want_g, facc);
+            if (full) node_task_im<R, NR, true, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
+            else node_task_im<R, NR, false, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
         }
     } else {
         if constexpr (NR >= 16) {
@@ -800,7 +812,7 @@ struct BlockShared {
 // contributions are added to G.  Starts and ends with a CTA barrier.
 template <typename R, int NR, int NI, bool SF, int XG, typename Acc>
 __device__ __forceinline__ R eval_tasks(const DevView &V, const Src &S, const R *xrow, const Acc &G, bool want_g,
-                                        int &s_ctr) {
+                                        int &s_ctr, bool want_f = true) {
     const int lane = threadIdx.x & 31;
     if (threadIdx.x == 0) s_ctr = 0;
     __syncthreads();
@@ -831,7 +843,7 @@ __device__ __forceinline__ R eval_tasks(const DevView &V, const Src &S, const R 
         } else {
             // node tasks carry their literals per lane in bits 16..23 (the batch
             // kernel also meets images built with 8 literals per lane)
-            node_dispatch<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc);
+            node_dispatch<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, want_g, facc, want_f);
         }
     }
     __syncthreads();
@@ -1005,7 +1017,8 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
     }
     const int iters = pgfp ? 0 : (step ? A.sp.T : 1);
     for (int it = 0; it < iters; ++it) {
-        R facc = eval_tasks<R, NR, NI, SF, XG>(V, S, xrow, G, want_g, s_ctr);
+        // a fixed step needs the gradient only; the objective is skipped on the node path
+        R facc = eval_tasks<R, NR, NI, SF, XG>(V, S, xrow, G, want_g, s_ctr, !step);
         if (!step) {
             if (A.f) {
                 const double tot = block_sum((double)facc, s_red);
