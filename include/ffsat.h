@@ -24,6 +24,9 @@
  *    device status word and reported by ffsat_sync_status().
  *  - The caller owns every x / f / g / sat / solved buffer; the library never
  *    frees them.  The library owns the instance and its device tables.
+ *  - An instance lives on the device it was loaded on (ffsat_options.device);
+ *    every entry point makes that device current for its own work and restores
+ *    the calling thread's current device before it returns.
  *  - An instance is read-only during ffsat_eval_grad / ffsat_check, which may run
  *    concurrently on different streams.  ffsat_step uses per-instance scratch for
  *    large n and ffsat_set_weights rewrites device tables: do not overlap those

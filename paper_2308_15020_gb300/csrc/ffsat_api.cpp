@@ -9,6 +9,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -176,6 +177,7 @@ struct ffsat_instance {
     ffsat_info info{};
     // resident clusters of the FP64 cluster step for CL = 2, 4, 8 (-1: not asked yet)
     int cluster_active[3] = {-1, -1, -1};
+    std::mutex cluster_mu;  // guards the lazy fill of cluster_active (steps may run on several host threads)
     // learned-proposal graph data (built on first use)
     unsigned char *d_graph = nullptr;
     GraphView graph{};
@@ -1166,7 +1168,8 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     // ---- device ----
     int dev = opt.device;
     if (dev < 0) CUDA_TRY(cudaGetDevice(&dev));
-    CUDA_TRY(cudaSetDevice(dev));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(dev));
     P->device = dev;
     CUDA_TRY(cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, dev));
     CUDA_TRY(cudaDeviceGetAttribute(&P->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
@@ -1293,7 +1296,8 @@ int ffsat_set_weights(ffsat_instance *I, const double *weights) {
         if (!(std::isfinite(weights[c]) && weights[c] >= 0.0)) return fail(FFSAT_ERR_WEIGHT, "constraint %d: bad weight", c);
     I->w.assign(weights, weights + I->m);
     fill_weights(I);
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     unsigned char *base = I->d_arena;
     for (int k = 0; k < I->n_images; ++k) {
         build_image(I, k);
@@ -1345,6 +1349,7 @@ static int step_cluster_size(ffsat_instance *I, int32_t B, int mode, size_t &sme
         const int cl = sizes[k];
         if (opt != 0 && cl != opt) continue;
         if (opt == 0 && ((int64_t)B * cl > I->num_sms || I->V64.n_task < cl)) continue;
+        std::lock_guard<std::mutex> lock(I->cluster_mu);
         if (I->cluster_active[k] < 0) {
             int active = 0;
             if (cluster_launcher(I->nr64)(I->V64, mode, FusedArgs{}, smem, g1_off, 1, cl, nullptr, &active) !=
@@ -1384,7 +1389,8 @@ int ffsat_eval_grad(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, 
     if (rc) return rc;
     if (B == 0) return FFSAT_OK;
     if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     const bool f64 = dtype == FFSAT_F64;
     FusedArgs a{};
     a.B = B;
@@ -1408,7 +1414,8 @@ int ffsat_eval_grad_plain64(ffsat_instance *I, int32_t B, const double *x, doubl
     if (B < 0) return fail(FFSAT_ERR_ARG, "B must be >= 0");
     if (B == 0) return FFSAT_OK;
     if (!x || !f || !g) return fail(FFSAT_ERR_ARG, "x, f and g are required");
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     int nl = 0;
     CUDA_TRY(launch_plain64(I->V64, B, x, f, g, I->n_node_ids, I->d_node_ids, I->n_closed_ids, I->d_closed_ids,
                             static_cast<cudaStream_t>(stream), &nl));
@@ -1428,7 +1435,8 @@ int ffsat_step(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat
     if (rc) return rc;
     if (B == 0) return FFSAT_OK;
     if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     const bool f64 = dtype == FFSAT_F64;
     const int mode = f64 ? I->smem_mode64 : I->smem_mode32;
     const size_t elem = f64 ? sizeof(double) : sizeof(float);
@@ -1446,7 +1454,9 @@ int ffsat_step(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat
     a.sp.epoch = args->epoch;
     a.sp.b_offset = args->b_offset;
     a.unsat_counts = args->unsat_counts;
-    if (mode != SMEM_FULL) {
+    // the gradient lives in shared memory in modes SMEM_FULL and SMEM_RES; the
+    // other two accumulate it in a [B, n] scratch
+    if (mode == SMEM_X || mode == SMEM_NONE) {
         const size_t need = (size_t)B * (size_t)I->n * elem;
         if (need > I->scratch_bytes) {
             if (I->d_scratch) CUDA_TRY(cudaFree(I->d_scratch));
@@ -1472,7 +1482,8 @@ int ffsat_step_noalloc(ffsat_instance *I, int32_t B, void *x, int32_t dtype, con
     if (rc) return rc;
     if (B == 0) return FFSAT_OK;
     if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     const bool f64 = dtype == FFSAT_F64;
     const int mode = f64 ? I->smem_mode64 : I->smem_mode32;
     const size_t elem = f64 ? sizeof(double) : sizeof(float);
@@ -1531,7 +1542,8 @@ int ffsat_step_pgfp(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const 
         return fail(FFSAT_ERR_ARG, "the line-search step needs x in shared memory (n = %d is too large)", I->n);
     if (B == 0) return FFSAT_OK;
     if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     const size_t elem = f64 ? sizeof(double) : sizeof(float);
     const size_t need = (size_t)B * (size_t)I->n * elem;
     FusedArgs a{};
@@ -1579,7 +1591,8 @@ int ffsat_check(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, uint
     if (rc) return rc;
     if (B == 0) return FFSAT_OK;
     if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     CUDA_TRY(launch_check(I->V32, dtype == FFSAT_F64, B, x, sat, n_unsat, nullptr, static_cast<cudaStream_t>(stream)));
     t_launches = 1;
     return FFSAT_OK;
@@ -1595,7 +1608,8 @@ int ffsat_unsat_counts(ffsat_instance *I, int32_t B, const void *x, int32_t dtyp
     if (I->m == 0) return FFSAT_OK;
     if (!U) return fail(FFSAT_ERR_ARG, "U is NULL");
     if (B > 0 && !x) return fail(FFSAT_ERR_ARG, "x is NULL");
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     CUDA_TRY(cudaMemsetAsync(U, 0, (size_t)I->m * sizeof(int32_t), s));
     CUDA_TRY(launch_check(I->V32, dtype == FFSAT_F64, B, x, nullptr, nullptr, U, s));
@@ -1610,7 +1624,8 @@ int ffsat_erwa_update(ffsat_instance *I, const int32_t *U, double alpha, void *s
     if (!(alpha >= 0.0 && alpha <= 1.0)) return fail(FFSAT_ERR_ARG, "alpha must lie in [0, 1]");
     if (I->m == 0) return FFSAT_OK;
     if (!U) return fail(FFSAT_ERR_ARG, "U is NULL");
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     unsigned char *base = I->d_arena;
     WeightSites W{};
     W.m = I->m;
@@ -1646,7 +1661,8 @@ static int rephase_impl(ffsat_instance *I, int32_t B, void *x, int32_t dtype, in
         return fail(FFSAT_ERR_ARG, "phase must be FFSAT_PHASE_ORIGINAL, _FLIPPED or _RANDOM");
     if (B == 0) return FFSAT_OK;
     if (!x) return fail(FFSAT_ERR_ARG, "x is NULL");
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     int nl = 0;
     CUDA_TRY(launch_rephase(dtype == FFSAT_F64, x, B, I->n, phase, solved, seed, epoch, b_offset, epoch_dev,
                             static_cast<cudaStream_t>(stream), &nl));
@@ -1669,7 +1685,8 @@ int ffsat_get_weights(ffsat_instance *I, double *weights) {
     t_err.clear();
     if (!I || !weights) return fail(FFSAT_ERR_ARG, "NULL argument");
     if (I->m == 0) return FFSAT_OK;
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     CUDA_TRY(cudaDeviceSynchronize());
     CUDA_TRY(cudaMemcpy(weights, I->d_arena + I->off_cons_wd, (size_t)I->m * sizeof(double), cudaMemcpyDeviceToHost));
     return FFSAT_OK;
@@ -1743,7 +1760,8 @@ int instance_graph(ffsat_instance *I, GraphView *out) {
     Arena A;
     const size_t o_rp = A.put(rp32), o_l = A.put(lp), o_vp = A.put(var_ptr), o_vo = A.put(occ), o_fv = A.put(fv),
                  o_fc = A.put(fc), o_id = A.put(inv_deg), o_il = A.put(inv_len);
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     CUDA_TRY(cudaMalloc(&I->d_graph, A.host.size()));
     CUDA_TRY(cudaMemcpy(I->d_graph, A.host.data(), A.host.size(), cudaMemcpyHostToDevice));
     GraphView &g = I->graph;
@@ -1916,7 +1934,8 @@ int ffsat_batch_create(ffsat_instance *const *insts, int32_t count, ffsat_batch 
     }
     bt->device = insts[0]->device;
     bt->num_sms = insts[0]->num_sms;
-    CUDA_TRY(cudaSetDevice(bt->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(bt->device));
     for (int v = 0; v < 2; ++v) {
         size_t smem = 0;
         int nr = 0;
@@ -1943,7 +1962,8 @@ int ffsat_batch_eval_grad(ffsat_batch *bt, const ffsat_batch_io *io, int32_t dty
     if (!bt || !io) return fail(FFSAT_ERR_ARG, "NULL argument");
     int rc = check_dtype(dtype);
     if (rc) return rc;
-    CUDA_TRY(cudaSetDevice(bt->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(bt->device));
     return batch_launch(bt, io, dtype, MODE_EVAL, nullptr, static_cast<cudaStream_t>(stream));
 }
 
@@ -1956,13 +1976,15 @@ int ffsat_batch_step(ffsat_batch *bt, const ffsat_batch_io *io, int32_t dtype, c
     if (!std::isfinite(args->lr)) return fail(FFSAT_ERR_ARG, "lr must be finite");
     int rc = check_dtype(dtype);
     if (rc) return rc;
-    CUDA_TRY(cudaSetDevice(bt->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(bt->device));
     return batch_launch(bt, io, dtype, MODE_STEP, args, static_cast<cudaStream_t>(stream));
 }
 
 void ffsat_batch_free(ffsat_batch *bt) {
     if (!bt) return;
-    cudaSetDevice(bt->device);
+    DeviceGuard dev_guard;
+    dev_guard.set(bt->device);
     if (bt->d_insts) cudaFree(bt->d_insts);
     if (bt->d_counter) cudaFree(bt->d_counter);
     if (bt->d_items) cudaFree(bt->d_items);
@@ -1973,7 +1995,8 @@ void ffsat_batch_free(ffsat_batch *bt) {
 int ffsat_sync_status(ffsat_instance *I, void *stream) {
     t_err.clear();
     if (!I) return fail(FFSAT_ERR_ARG, "instance is NULL");
-    CUDA_TRY(cudaSetDevice(I->device));
+    DeviceGuard dev_guard;
+    CUDA_TRY(dev_guard.set(I->device));
     CUDA_TRY(cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
     int32_t st = 0;
     CUDA_TRY(cudaMemcpy(&st, I->d_status, sizeof(st), cudaMemcpyDeviceToHost));
@@ -1991,7 +2014,8 @@ int ffsat_instance_info(const ffsat_instance *I, ffsat_info *info) {
 
 void ffsat_free(ffsat_instance *I) {
     if (!I) return;
-    cudaSetDevice(I->device);
+    DeviceGuard dev_guard;
+    dev_guard.set(I->device);
     if (I->d_graph) cudaFree(I->d_graph);
     if (I->d_arena) cudaFree(I->d_arena);
     if (I->d_status) cudaFree(I->d_status);

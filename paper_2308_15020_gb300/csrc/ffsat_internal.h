@@ -39,6 +39,25 @@ enum : int32_t { SMEM_FULL = 0, SMEM_X = 1, SMEM_NONE = 2, SMEM_RES = 3 };
 // generic alpha + beta y factors (paper form).
 enum : int32_t { NODE_FORM_IMAG = 0, NODE_FORM_GENERIC = 1 };
 
+// Makes a device current for the lifetime of the guard and restores the
+// caller's current device when it ends, so that no entry point leaves the
+// calling thread on another device.
+struct DeviceGuard {
+    int prev = -1;
+    cudaError_t set(int device) {
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e != cudaSuccess) {
+            prev = -1;
+            return e;
+        }
+        return prev == device ? cudaSuccess : cudaSetDevice(device);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
 // Device status bits.
 enum : int32_t { STATUS_NAN = 1, STATUS_OTHER = 2 };
 

@@ -2,30 +2,36 @@
 #pragma once
 #include <map>
 #include <mutex>
+#include <utility>
 
 #include "fused_kernel.cuh"
 
 namespace ffsat {
 namespace dev {
 
-// Raise a kernel's dynamic shared-memory limit to at least `smem`.  The limit
-// belongs to the kernel, not to an instance, so it only ever grows: a later,
-// smaller instance must not lower it below what an earlier one launches with.
-// The first request always sets the attribute: the default limit is 48 KB less
-// the kernel's static shared memory, not 48 KB.
+// Raise a kernel's dynamic shared-memory limit to at least `smem` on the
+// current device.  The limit belongs to the kernel in one device's context, not
+// to an instance, so it only ever grows per (device, kernel): a later, smaller
+// instance must not lower it below what an earlier one launches with, and an
+// instance on another device sets it there too.  The first request on a device
+// always sets the attribute: the default limit is 48 KB less the kernel's static
+// shared memory, not 48 KB.
 inline std::mutex &smem_limit_mutex() {
     static std::mutex mu;
     return mu;
 }
-inline std::map<const void *, size_t> &smem_limits() {
-    static std::map<const void *, size_t> limits;
+inline std::map<std::pair<int, const void *>, size_t> &smem_limits() {
+    static std::map<std::pair<int, const void *>, size_t> limits;
     return limits;
 }
 
 template <typename Kernel>
 cudaError_t raise_smem_limit(Kernel k, size_t smem) {
     std::lock_guard<std::mutex> lock(smem_limit_mutex());
-    size_t &current = smem_limits()[reinterpret_cast<const void *>(k)];
+    int dev = 0;
+    const cudaError_t ge = cudaGetDevice(&dev);
+    if (ge != cudaSuccess) return ge;
+    size_t &current = smem_limits()[{dev, reinterpret_cast<const void *>(k)}];
     if (current != 0 && smem <= current) return cudaSuccess;
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) current = smem;

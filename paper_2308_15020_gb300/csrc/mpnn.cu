@@ -597,14 +597,16 @@ int32_t ffsat_mpnn_num_params(const ffsat_mpnn *M) { return M ? M->n_params : 0;
 
 int ffsat_mpnn_get_params(const ffsat_mpnn *M, float *host) {
     if (!M || !host) return set_error(FFSAT_ERR_ARG, "NULL argument");
-    MP_TRY(cudaSetDevice(M->device));
+    ffsat::DeviceGuard dev_guard;
+    MP_TRY(dev_guard.set(M->device));
     MP_TRY(cudaMemcpy(host, M->p, M->n_params * sizeof(float), cudaMemcpyDeviceToHost));
     return FFSAT_OK;
 }
 
 int ffsat_mpnn_set_params(ffsat_mpnn *M, const float *host) {
     if (!M || !host) return set_error(FFSAT_ERR_ARG, "NULL argument");
-    MP_TRY(cudaSetDevice(M->device));
+    ffsat::DeviceGuard dev_guard;
+    MP_TRY(dev_guard.set(M->device));
     MP_TRY(cudaMemcpy(M->p, host, M->n_params * sizeof(float), cudaMemcpyHostToDevice));
     to_bf16<<<blocks_for(M->n_params, 256), 256>>>(M->p, M->pb, M->n_params);
     MP_TRY(cudaDeviceSynchronize());
@@ -616,7 +618,8 @@ int ffsat_mpnn_forward(ffsat_mpnn *M, ffsat_instance *inst, float *x0, void *str
     GraphView G;
     int rc = instance_graph(inst, &G);
     if (rc) return rc;
-    MP_TRY(cudaSetDevice(M->device));
+    ffsat::DeviceGuard dev_guard;
+    MP_TRY(dev_guard.set(M->device));
     return run(M, G, nullptr, nullptr, x0, static_cast<cudaStream_t>(stream));
 }
 
@@ -626,7 +629,8 @@ int ffsat_mpnn_loss_grad(ffsat_mpnn *M, ffsat_instance *inst, const float *targe
     GraphView G;
     int rc = instance_graph(inst, &G);
     if (rc) return rc;
-    MP_TRY(cudaSetDevice(M->device));
+    ffsat::DeviceGuard dev_guard;
+    MP_TRY(dev_guard.set(M->device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     rc = run(M, G, target, loss, x0, s);
     if (rc) return rc;
@@ -639,7 +643,8 @@ int ffsat_mpnn_loss_grad(ffsat_mpnn *M, ffsat_instance *inst, const float *targe
 
 int ffsat_mpnn_adam_step(ffsat_mpnn *M, float lr, void *stream) {
     if (!M || !(lr >= 0.f)) return set_error(FFSAT_ERR_ARG, "bad argument");
-    MP_TRY(cudaSetDevice(M->device));
+    ffsat::DeviceGuard dev_guard;
+    MP_TRY(dev_guard.set(M->device));
     M->adam_t += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - std::pow(b1, (float)M->adam_t), c2 = 1.f - std::pow(b2, (float)M->adam_t);
@@ -662,7 +667,8 @@ int ffsat_restart_from_proposal(ffsat_instance *inst, int32_t B, void *x, int32_
     GraphView G;
     rc = instance_graph(inst, &G);
     if (rc) return rc;
-    MP_TRY(cudaSetDevice(G.device));
+    ffsat::DeviceGuard dev_guard;
+    MP_TRY(dev_guard.set(G.device));
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const unsigned grid = (unsigned)std::min(B, 65535 * 16);
     if (dtype == FFSAT_F32)
@@ -677,7 +683,8 @@ int ffsat_restart_from_proposal(ffsat_instance *inst, int32_t B, void *x, int32_
 
 void ffsat_mpnn_free(ffsat_mpnn *M) {
     if (!M) return;
-    cudaSetDevice(M->device);
+    ffsat::DeviceGuard dev_guard;
+    dev_guard.set(M->device);
     for (void *a : M->allocs) cudaFree(a);
     if (M->p) cudaFree(M->p);
     if (M->g) cudaFree(M->g);

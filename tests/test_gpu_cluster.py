@@ -26,20 +26,23 @@ def _run(inst, x_np, cluster, **kw):
 
 
 def _instances():
-    # (name, instance, iterations per call)
+    # (name, instance, iterations per call, FP64 shared-memory layout: 3 = the
+    # resident image beside x and the gradient, 0 = x and the gradient only)
     return [
-        ("3sat_n100", gen.uniform_3sat_100(3), 40),          # clause path only
-        ("card_n100", gen.bench1_cardinality(100, 7), 40),   # node path (20-literal at-least-10)
-        ("mixed", mixed_instance(33, n=700), 12),            # every path, constants, long constraints
-        ("cnf_xor", gen.cnf_xor_2000(2), 40),                # clause and product paths, resident image
+        ("3sat_n100", gen.uniform_3sat_100(3), 40, 3),            # clause path only
+        ("card_n100", gen.bench1_cardinality(100, 7), 40, 3),     # node path (20-literal at-least-10)
+        ("mixed", mixed_instance(33, n=700), 12, 3),              # every path, constants, long constraints
+        ("cnf_xor", gen.cnf_xor_2000(2), 40, 3),                  # clause and product paths, resident image
+        ("3sat_n5000", gen.random_ksat(5000, 21000, 3, 4), 10, 0),  # image too large: x and g only
     ]
 
 
-@pytest.mark.parametrize("name,inst,T", _instances(), ids=lambda v: v if isinstance(v, str) else "")
+@pytest.mark.parametrize("name,inst,T,mode", _instances(), ids=lambda v: v if isinstance(v, str) else "")
 @pytest.mark.parametrize("B", [1, 7, 32])
-def test_cluster_step_matches_one_cta_and_oracle(name, inst, T, B):
+def test_cluster_step_matches_one_cta_and_oracle(name, inst, T, mode, B):
     x0 = gen.uniform_points(B, inst.n, 11 + B, dtype=np.float64)
-    xa, sa, na, Ua, cla, _ = _run(inst, x0, 0, T=T, lr=0.05, seed=5, epoch=2, restart=False)
+    xa, sa, na, Ua, cla, h = _run(inst, x0, 0, T=T, lr=0.05, seed=5, epoch=2, restart=False)
+    assert h.info()["smem_mode_f64"] == mode  # both layouts of the cluster kernel are covered
     xb, sb, nb, Ub, clb, _ = _run(inst, x0, 1, T=T, lr=0.05, seed=5, epoch=2, restart=False)
     assert clb == 1
     assert cla > 1, "the automatic choice kept one CTA per point"

@@ -48,6 +48,30 @@ def test_noalloc_step_matches_step_two_calls():
         assert torch.equal(sa, sb) and torch.equal(na, nb)
 
 
+def test_noalloc_first_call_allocates_no_device_memory():
+    """On a fresh instance that needs scratch, the first allocation-free call
+    leaves the device's free memory unchanged (ffsat_step would allocate B * n
+    values there)."""
+    from paper_2308_15020_gb300 import ffsat
+
+    n, B = 30000, 6
+    inst = _scratch_instance(n)
+    h = ffsat.Instance(inst)
+    assert h.info()["smem_mode_f32"] in (1, 2)
+    x = torch.from_numpy(gen.uniform_points(B, n, 22)).cuda()
+    h.step_noalloc(x, T=1, lr=0.05, seed=1, restart=False)  # the static buffer's address is looked up here
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    h2 = ffsat.Instance(inst)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    h2.step_noalloc(x, T=1, lr=0.05, seed=1, restart=False)
+    torch.cuda.synchronize()
+    free2, _ = torch.cuda.mem_get_info()
+    assert free2 == free1, (free1 - free2)
+    assert free0 - free1 >= 0  # loading the instance may allocate; the step does not
+
+
 def test_noalloc_rejects_sizes_beyond_static_scratch():
     from paper_2308_15020_gb300 import ffsat
 
