@@ -1,10 +1,11 @@
 """Shared helpers for the GPU parity tests: instances, tolerances, comparisons.
 
-Tolerance (FP32 path).  Every constraint value FE_c lies in [-1, 1] and the
-stable node form keeps every factor and partial product inside the unit disc,
-so the FP32 rounding error of one constraint is absolute, of order
-L * eps32 * sum_j |d_j| (at most ~1e-5 for L = 512), not relative to the
-possibly tiny value of one term.  We therefore read the 1e-4 relative
+Tolerance (FP32 path).  Every constraint value FE_c lies in [-1, 1].  The
+node path evaluates each node's product prod_i (1 + i t_j y_i) with a relative
+(norm-wise) rounding error of order L * eps32 and scales it so that the node's
+term C_j Q_j has modulus at most |c_j|, so the FP32 rounding error of one
+constraint is absolute, of order L * eps32 * sum_j |c_j| (at most ~1e-5 for
+L = 512), not relative to the possibly tiny value of one term.  We therefore read the 1e-4 relative
 tolerance of the FP32 path against the condition scale of each sum of signed
 terms:
     |f - f*| <= 1e-4 * max(|f*|, sum_c w_c |FE_c*|)

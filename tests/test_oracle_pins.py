@@ -520,3 +520,56 @@ def test_pgfp_stops_below_the_minimum_step():
     assert np.all(its == 1) and np.all(eta <= 1e-13)
     with pytest.raises(ValueError):
         O.step_pgfp(inst, x0, T=5, eta0=0.1, beta=1.5)
+
+
+# ---------------------------------------------------------------------------------------------
+# The tolerance scales every parity test divides by
+# ---------------------------------------------------------------------------------------------
+
+
+def _fe_corner_expectation(ctype, param, y):
+    """FE at y as the expectation of the truth value v(#True) over independent
+    literals that are True (-1) with probability (1 - y_i) / 2: the sum over all
+    2^L corners (Thm. "Walsh Transform" read as an expectation)."""
+    L = len(y)
+    tot = 0.0
+    for z in itertools.product((-1.0, 1.0), repeat=L):
+        s = sum(1 for zi in z if zi < 0)
+        sat = s >= 1 if ctype == O.OR else ((s % 2) == (param % 2) if ctype == O.XOR else s >= param)
+        p = 1.0
+        for yi, zi in zip(y, z):
+            p *= (1.0 + yi * zi) / 2.0
+        tot += (-1.0 if sat else 1.0) * p
+    return tot
+
+
+@pytest.mark.parametrize("floor", [0.0, 1e-2, 0.3])
+def test_eval_scale_against_direct_restatement(floor):
+    """orc_eval_scale: sf_b = sum_c w_c |FE_c|, A[b, v] = sum_{c containing v}
+    w_c max(|dFE_c/dy_v|, floor for at-least-K constraints), restated from
+    corner sums (FE) and exact central differences (the derivative of a
+    multilinear polynomial along one coordinate is half its difference between
+    y_v = +1 and y_v = -1).  A dropped weight, a lost absolute value, a floor on
+    the wrong type or a gradient credited to the wrong variable fails here."""
+    n = 7
+    cons = [(O.OR, 0, [1, -2, 3]), (O.XOR, 1, [2, 4, -5, 6]), (O.ATLEAST, 2, [1, 3, -4, 5, 7]),
+            (O.ATLEAST, 0, [2, 6]), (O.XOR, 0, [-7]), (O.ATLEAST, 5, [1, -2, 3])]
+    w = np.array([0.5, 1.5, 2.0, 0.75, 1.25, 3.0])
+    inst = gen.from_lists(n, cons, w)
+    x = np.random.default_rng(5).uniform(-1, 1, (3, n))
+    sf, A = O.eval_scale(inst, x, floor)
+    for b in range(3):
+        sf_want = 0.0
+        A_want = np.zeros(n)
+        for (ctype, param, lits), wc in zip(cons, w):
+            sg = np.sign(lits)
+            vs = np.abs(lits) - 1
+            y = sg * x[b, vs]
+            sf_want += wc * abs(_fe_corner_expectation(ctype, param, y))
+            for i in range(len(lits)):
+                hi, lo = y.copy(), y.copy()
+                hi[i], lo[i] = 1.0, -1.0
+                d = 0.5 * (_fe_corner_expectation(ctype, param, hi) - _fe_corner_expectation(ctype, param, lo))
+                A_want[vs[i]] += wc * max(abs(d), floor if ctype == O.ATLEAST else 0.0)
+        assert sf[b] == pytest.approx(sf_want, rel=1e-12, abs=1e-15)
+        assert np.allclose(A[b], A_want, rtol=1e-12, atol=1e-15)
