@@ -1188,6 +1188,63 @@ def run_ours(args, rank: int, world: int, local_rank: int):
         dist.destroy_process_group()
 
 
+def batch_autotune_record(args, insts, hs, bt, xs_host, B: int, T: int, lr: float, flush, t_load: float):
+    """The load-time autotuner on the uneven batch: the same batch step (restarts
+    off, so both do the same work) timed with every instance's default tile
+    choices and with the tuned ones, and the choices made."""
+    import torch
+
+    from paper_2308_15020_gb300 import ffsat
+
+    t0 = time.perf_counter()
+    hs_def = [ffsat.Instance(i) for i in insts]
+    t_def = time.perf_counter() - t0
+    bt_def = ffsat.Batch(hs_def)
+    stream = torch.cuda.current_stream()
+
+    def timed(batch, reps):
+        xs = [x.cuda() for x in xs_host]
+        batch.step(xs, T=T, lr=lr, seed=7, epoch=0, restart=False)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for r in range(reps):
+            xs = [x.cuda() for x in xs_host]
+            flush.zero_()
+            s_, e_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s_.record(stream)
+            batch.step(xs, T=T, lr=lr, seed=7, epoch=r + 1, restart=False, stream=stream)
+            e_.record(stream)
+            torch.cuda.synchronize()
+            tot += s_.elapsed_time(e_)
+        return tot / reps
+
+    reps = max(2, min(args.steps, 5))
+    ms_def = timed(bt_def, reps)
+    ms_tun = timed(bt, reps)
+    choices = {}
+    cand = cached = 0
+    for h in hs:
+        inf = h.info()
+        key = f"node_r {inf['node_r']} shape {inf['tune_shape']} clause_k {inf['tune_clause_k']}"
+        choices[key] = choices.get(key, 0) + 1
+        cand += inf["tune_candidates"]
+        cached += inf["tune_cached"]
+    th_tun, us384, us512 = bt.threads()
+    th_def = bt_def.threads()[0]
+    bt_def.free()
+    for h in hs_def:
+        h.free()
+    return {"default_ms_per_step": ms_def, "tuned_ms_per_step": ms_tun, "speedup": ms_def / ms_tun,
+            "batch_threads_per_cta": {"tuned": th_tun, "default": th_def, "probe_us_384": us384,
+                                      "probe_us_512": us512},
+            "steps_timed_each": reps, "choices": choices, "candidates_timed": cand, "cached_instances": cached,
+            "load_s_tuned": t_load, "load_s_default": t_def,
+            "search": "per instance, FP32: node literals per lane and segment shape (cost model, fewest lanes, "
+                      "fewest slots, 8-literal family), clause groups per task (auto, 1, 2, 4), points per CTA "
+                      "(1, 2); each candidate timed on two points per SM, kept when >= 1% faster; per batch: "
+                      "threads per CTA of the FP32 batch kernel (384, 512) timed on two points per instance"}
+
+
 def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
     """Configuration 4: all instances' points in one persistent launch per step."""
     import torch
@@ -1195,7 +1252,10 @@ def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
     from paper_2308_15020_gb300 import ffsat
 
     insts = build(0)
-    hs = [ffsat.Instance(i) for i in insts]
+    tuned = not args.no_autotune
+    t_load = time.perf_counter()
+    hs = [ffsat.Instance(i, autotune=tuned) for i in insts]
+    t_load = time.perf_counter() - t_load
     bt = ffsat.Batch(hs)
     xs_host = [torch.from_numpy(gen.uniform_points(B, i.n, 2000 + 97 * k + rank)).pin_memory()
                for k, i in enumerate(insts)]
@@ -1288,6 +1348,7 @@ def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
         if dist:
             dist.destroy_process_group()
         return
+    tune_rec = batch_autotune_record(args, insts, hs, bt, xs_host, B, T, lr, flush, t_load) if tuned else None
     flops = bytes_ = 0.0
     for i in insts:
         fl, by, _, _ = algorithmic_work(instance_stats(i), B, T)
@@ -1320,6 +1381,8 @@ def run_ours_batch(args, rank, world, local_rank, dist, build, B, T, lr):
         "gpu_launches": launches_per_step * args.steps, "clocks": clk, "alu_peaks_measured": alu,
         "kernel_source_hash": kernel_source_hash(),
     }
+    if tune_rec is not None:
+        line["autotune"] = tune_rec
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -1344,6 +1407,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="uneven_batch: load the instances with default tiles")
     ap.add_argument("--no-node-path", action="store_true",
                     help="default line: skip the DFT node-path record (CNF + at-least-K n=20000)")
     ap.add_argument("--node-path-steps", type=int, default=5, help="timed steps of the node-path record")

@@ -78,8 +78,12 @@ typedef struct ffsat_options {
     /* Literals per lane in the node kernel: 0 = automatic (autotuned when
      * `autotune` is set), else 8 or 16. */
     int32_t node_r;
-    /* 1: time the candidate kernel variants on the device at load and keep the
-     * fastest (costs a few milliseconds per load). */
+    /* 1: autotune the FP32 tile choices at load: time one evaluation on two
+     * points per SM for each candidate of a coordinate search (node literals per
+     * lane and segment shape, clause groups per task, points per CTA) and keep
+     * the fastest; the choice is cached by instance shape, so later instances of
+     * the same shape load without timing.  Costs up to about ten evaluations per
+     * newly seen shape. */
     int32_t autotune;
     /* CUDA device ordinal, -1 = the current device. */
     int32_t device;
@@ -127,12 +131,20 @@ typedef struct ffsat_info {
     int32_t threads_f32;   /* threads per CTA of the fused kernel */
     int64_t node_lane_work; /* sum over node constraints of nodes x (lanes x R) per point */
     int64_t device_bytes;  /* device memory held by the instance */
-    int32_t autotuned;     /* 1 if node_r was chosen by timing candidates at load */
-    float autotune_us[2];  /* measured eval time of the candidates (node R 16/12, node R 8), microseconds */
+    int32_t autotuned;     /* 1 if the FP32 tile choices were set by the autotuner (ffsat_options.autotune) */
+    float autotune_us[2];  /* FP32 evaluation time on the autotuner's probe batch (two points per SM),
+                              microseconds: [0] the default choices, [1] the chosen ones */
     int32_t n_xor2;        /* XOR constraints of <= 2 literals (thread-per-constraint records, like clauses) */
     int32_t pad;
     int64_t smem_bytes_f32; /* dynamic shared memory per CTA of the fused kernel */
     int64_t smem_bytes_f64;
+    /* FP32 tile choices (defaults unless autotuned) */
+    int32_t tune_shape;       /* node segment shape: 0 cost model, 1 fewest lanes, 2 fewest literal slots */
+    int32_t tune_clause_k;    /* clause groups of 32 per clause task: 0 automatic, else 1, 2 or 4 */
+    int32_t tune_pts_per_cta; /* points per CTA of the fused kernel */
+    int32_t tune_candidates;  /* candidate images timed at load (0 when the choice came from the cache) */
+    int32_t tune_cached;      /* 1 if an earlier instance of the same shape supplied the choice */
+    int32_t pad2;
 } ffsat_info;
 
 /* Fill `opt` with the defaults (stable form, closed forms for OR/XOR,
@@ -325,8 +337,15 @@ typedef struct ffsat_batch_io {
  * device counter; every point runs exactly as in ffsat_eval_grad / ffsat_step of
  * its instance (same shared-memory mode and constraint layout).  The instances
  * must outlive the batch.  Configuration 4 of the benchmark ("uneven instances
- * in one launch") is this call. */
+ * in one launch") is this call.  When every instance was loaded with
+ * ffsat_options.autotune and the batch has FP32 node-path work, the CTA width of
+ * its FP32 kernel (384 or 512 threads) is chosen here by timing one evaluation
+ * of two points per instance at each width (synchronous); otherwise 512. */
 int ffsat_batch_create(ffsat_instance *const *insts, int32_t count, ffsat_batch **out);
+
+/* Threads per CTA of the batch's kernel for dtype, and the FP32 probe times of
+ * the two widths in microseconds (us384, us512: 0 when not timed; may be NULL). */
+int ffsat_batch_threads(const ffsat_batch *bt, int32_t dtype, int32_t *threads, float *us384, float *us512);
 
 /* ffsat_eval_grad for every instance of the batch in one launch (plus one
  * memset of the work counter).  io: host array of `count` entries. */

@@ -121,6 +121,17 @@ struct TaskSet {
     int node_r = 0;
 };
 
+// Tile choices of one resident image: the defaults, or what the autotuner
+// measured fastest for the instance.
+struct Knobs {
+    int32_t shape = 0;        // node segment shape: 0 cost model, 1 fewest lanes, 2 fewest literal slots
+    int32_t clause_k = 0;     // clause groups of 32 per clause task: 0 automatic, else 1, 2 or 4
+    int32_t pts_per_cta = 1;  // points per CTA of the fused kernel (grid = ceil(B / pts_per_cta))
+    bool operator==(const Knobs &o) const {
+        return shape == o.shape && clause_k == o.clause_k && pts_per_cta == o.pts_per_cta;
+    }
+};
+
 }  // namespace
 
 struct ffsat_instance {
@@ -142,7 +153,7 @@ struct ffsat_instance {
     std::vector<int32_t> seg_lits;
     int n_node_seg = 0;
     int32_t pad_node = 0;        // padding literal of node segments (dummy n or n + 1)
-    int nr[3] = {0, 0, 0};       // node R of each image
+    int nr[2] = {0, 0};          // node R family of each image (16: 16/12/8 per segment, 8, or 0)
     std::vector<double> clause_wd;
     std::vector<double> seg_wd;
     std::vector<double> cons_wd;
@@ -151,13 +162,17 @@ struct ffsat_instance {
     float fix_s1 = 1.0f, fix_s2 = 1.0f, fix_i1 = 1.0f, fix_i12 = 1.0f;
     std::vector<int64_t> row_ptr;  // host copy of the CSR (fixed-point scales)
     std::vector<int32_t> lits_in;
-    // resident images (index 0: FP32 task list, 1: FP64 task list, 2: the FP32
-    // autotune candidate that lost, kept so that set_weights stays consistent)
+    // resident images (index 0: FP32 task list, 1: FP64 task list), each with the
+    // tile choices it was built with and its own device allocation
     int n_images = 2;
-    std::vector<int4> tasks[3];
-    std::vector<int4> image[3];
-    int32_t img_off[3][4] = {{0}};  // tasks, clauses, segmeta, seg_lits (int4 units)
-    size_t off_image[3] = {0, 0, 0};
+    std::vector<int4> tasks[2];
+    std::vector<int4> image[2];
+    Knobs knobs[2];
+    int32_t img_off[2][4] = {{0}};  // tasks, clauses, segmeta, seg_lits (int4 units)
+    int4 *d_img[2] = {nullptr, nullptr};
+    // what the task lists are built from (kept for the autotuner's rebuilds)
+    std::vector<int32_t> seg_len;
+    int n_clause_pad = 0, n_xor2_pad = 0, max_node_len = 0;
     // device
     unsigned char *d_arena = nullptr;
     size_t arena_bytes = 0;
@@ -239,12 +254,17 @@ inline int seg_lanes(int L, int R) { return std::max(1, pow2_at_least((L + R - 1
 // normalisation, division and scales, and per butterfly level three shuffles,
 // an exponent add and a complex product), G * (14 NR + 12 + 10 log2 G) for the
 // generic one.
-inline int node_nr(int L, int nr_max, bool imag) {
+// The autotuner may replace the model by another segment shape: the fewest
+// lanes per segment (shape 1; ties to fewer literal slots) or the fewest literal
+// slots G * NR (shape 2; ties to fewer lanes).
+inline int node_nr(int L, int nr_max, bool imag, int shape = 0) {
     if (nr_max < 16) return nr_max;
     auto cost = [&](int nr) {
         const int G = seg_lanes(L, nr);
         if (G > 32) return 1e30;
         const double lg = std::log2((double)G);
+        if (shape == 1) return (double)G * 1024.0 + (double)(G * nr);
+        if (shape == 2) return (double)(G * nr) * 64.0 + (double)G;
         return imag ? (double)G * (7.0 * nr + 58.0 + 8.0 * lg) : (double)G * (14.0 * nr + 12.0 + 10.0 * lg);
     };
     int best = 16;
@@ -426,7 +446,7 @@ int clause_groups_per_task(int groups, int other_tasks, int warps) {
 }
 
 void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clause, int n_xor2, int node_r,
-                 int warps, bool imag, TaskSet &ts) {
+                 int warps, bool imag, const Knobs &kn, TaskSet &ts) {
     ts.tasks.clear();
     ts.node_r = node_r;
     auto group = [&](int first, int count, int kind, int R) {
@@ -434,13 +454,13 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
         const int end = first + count;
         while (i < end) {
             const int L = seg_len[i];
-            const int nr = kind == TASK_NODE ? node_nr(L, R, imag) : R;
+            const int nr = kind == TASK_NODE ? node_nr(L, R, imag, kn.shape) : R;
             const int G = seg_lanes(L, nr);
             const int S = 32 / G;
             int k = 0;
             while (k < S && i + k < end) {
                 const int Lk = seg_len[i + k];
-                const int nk = kind == TASK_NODE ? node_nr(Lk, R, imag) : R;
+                const int nk = kind == TASK_NODE ? node_nr(Lk, R, imag, kn.shape) : R;
                 if (nk != nr || seg_lanes(Lk, nk) != G) break;
                 ++k;
             }
@@ -455,7 +475,7 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
     // (1, 2 or 4 groups: the kernel has one unrolled body for each; a tail that is not
     // a whole task is split into smaller powers of two)
     // records [0, n_clause) are clauses, [n_clause, n_clause + n_xor2) short XORs
-    const int k = clause_groups_per_task((n_clause + n_xor2) / 32, (int)ts.tasks.size(), warps);
+    const int k = kn.clause_k ? kn.clause_k : clause_groups_per_task((n_clause + n_xor2) / 32, (int)ts.tasks.size(), warps);
     for (int part = 0; part < 2; ++part) {
         const int kind = part == 0 ? TASK_CLAUSE : TASK_XOR2;
         const int end = part == 0 ? n_clause : n_clause + n_xor2;
@@ -696,7 +716,7 @@ void build_image(ffsat_instance *I, int k) {
     for (size_t s = 0; s < I->seg_info.size(); ++s) {
         const int4 si = I->seg_info[s];
         const bool node = (int)s < I->n_node_seg;
-        const int R = node ? node_nr(si.y, nr, I->opt.form == FFSAT_FORM_STABLE) : kProdR;
+        const int R = node ? node_nr(si.y, nr, I->opt.form == FFSAT_FORM_STABLE, I->knobs[k].shape) : kProdR;
         const int G = seg_lanes(si.y, R);
         const int32_t pad = node ? I->pad_node : I->n;
         const int32_t off = (int32_t)lits.size();
@@ -860,7 +880,7 @@ void bank_order(std::vector<int4> &cls, std::vector<int32_t> &cid) {
 // DevView of image k on top of the shared part V.
 DevView view_for_image(ffsat_instance *P, const DevView &V, int k) {
     DevView W = V;
-    const int4 *img = reinterpret_cast<const int4 *>(P->d_arena + P->off_image[k]);
+    const int4 *img = P->d_img[k];
     W.res_image = img;
     W.res_int4 = (int32_t)P->image[k].size();
     W.res_off_tasks = P->img_off[k][0];
@@ -875,71 +895,233 @@ DevView view_for_image(ffsat_instance *P, const DevView &V, int k) {
     return W;
 }
 
-// Time the FP32 evaluation of images 0 (node R 16/12) and 2 (node R 8) on a
-// probe batch of one point per SM and keep the faster as image 0.
+// Warp tasks and resident image k (0: FP32, 1: FP64) from the instance's node R
+// family nr[k] and tile choices knobs[k].
+void rebuild_image(ffsat_instance *P, int k) {
+    TaskSet ts;
+    build_tasks(P->seg_len, P->n_node_seg, P->n_clause_pad, P->n_xor2_pad, P->nr[k],
+                fused_threads(k == 1, P->nr[k]) / 32, P->opt.form == FFSAT_FORM_STABLE, P->knobs[k], ts);
+    P->tasks[k] = ts.tasks;
+    build_image(P, k);
+}
+
+// Every literal the kernels will index must name a variable or one of the two dummies.
+int check_image(const ffsat_instance *P, int k) {
+    const int32_t *w = reinterpret_cast<const int32_t *>(P->image[k].data());
+    for (size_t i = (size_t)P->img_off[k][1] * 4; i < (size_t)P->img_off[k][2] * 4; ++i)
+        if ((i & 3) != 3 && ((uint32_t)w[i] & 0x7fffffffu) > (uint32_t)P->n + 1)
+            return fail(FFSAT_ERR_PARAM, "internal: clause record %zu out of range", i / 4);
+    for (size_t i = (size_t)P->img_off[k][3] * 4; i < P->image[k].size() * 4; ++i)
+        if (((uint32_t)w[i] & 0x7fffffffu) > (uint32_t)P->n + 1)
+            return fail(FFSAT_ERR_PARAM, "internal: segment literal %zu out of range", i);
+    return FFSAT_OK;
+}
+
+// (Re)allocate and upload resident image k (the device must be current).
+int upload_image(ffsat_instance *P, int k) {
+    if (P->d_img[k]) CUDA_TRY(cudaFree(P->d_img[k]));
+    P->d_img[k] = nullptr;
+    const size_t bytes = P->image[k].size() * sizeof(int4);
+    CUDA_TRY(cudaMalloc(&P->d_img[k], std::max<size_t>(bytes, 16)));
+    CUDA_TRY(cudaMemcpy(P->d_img[k], P->image[k].data(), bytes, cudaMemcpyHostToDevice));
+    return FFSAT_OK;
+}
+
+// Tile choices found by earlier loads, keyed by the instance's shape (sizes,
+// path counts, longest node constraint, node work, form): an instance of the
+// same shape reuses them without timing.
+using TuneKey = std::array<int64_t, 10>;
+struct TuneChoice {
+    int nr;
+    Knobs kn;
+    float default_us, best_us;
+    int candidates;
+};
+std::mutex &tune_mutex() {
+    static std::mutex mu;
+    return mu;
+}
+std::map<TuneKey, TuneChoice> &tune_cache() {
+    static std::map<TuneKey, TuneChoice> cache;
+    return cache;
+}
+TuneKey tune_key(const ffsat_instance *P) {
+    int64_t node_work = 0;
+    for (int s = 0; s < P->n_node_seg; ++s) node_work += (int64_t)((P->seg_len[s] + 1) / 2 + 1) * P->seg_len[s];
+    return {P->n, P->m, P->nnz, P->n_node_seg, (int64_t)P->seg_len.size() - P->n_node_seg, P->n_clause_pad,
+            P->n_xor2_pad, P->max_node_len, node_work, P->opt.form};
+}
+
+// The FP32 autotuner.  It times one evaluation of F and grad F
+// (min over three launches after a warm-up) on a probe batch of two points per
+// SM, for each candidate image in a coordinate search, and keeps the fastest:
+//   1. node literals per lane: the 16/12/8 family with the cost-model segment
+//      shape (default), the fewest lanes per segment or the fewest literal slots,
+//      and the 8-literal family (constraints of at most 256 literals);
+//   2. clause groups of 32 per clause task: automatic (default), 1, 2 or 4;
+//   3. points per CTA: one (default) or two, which halves the copies of a
+//      shared-memory-resident image.
+// A candidate replaces the best only when at least 1% faster.  The choice is
+// cached by instance shape.
 int autotune(ffsat_instance *P, const DevView &V) {
-    const int B = P->num_sms;
-    const size_t elems = (size_t)B * (size_t)P->n;
-    std::vector<float> hx(elems);
-    uint64_t st = 0x9E3779B97F4A7C15ull;
-    for (size_t i = 0; i < elems; ++i) {
-        st = st * 6364136223846793005ull + 1442695040888963407ull;
-        hx[i] = (float)((double)(st >> 40) / (double)(1ull << 23) - 1.0);
+    const TuneKey key = tune_key(P);
+    {
+        std::lock_guard<std::mutex> lock(tune_mutex());
+        auto it = tune_cache().find(key);
+        if (it != tune_cache().end()) {
+            const TuneChoice &c = it->second;
+            if (c.nr != P->nr[0] || !(c.kn == P->knobs[0])) {
+                P->nr[0] = c.nr;
+                P->knobs[0] = c.kn;
+                rebuild_image(P, 0);
+                int rc = check_image(P, 0);
+                if (rc != FFSAT_OK) return rc;
+                rc = upload_image(P, 0);
+                if (rc != FFSAT_OK) return rc;
+            }
+            P->info.autotune_us[0] = c.default_us;
+            P->info.autotune_us[1] = c.best_us;
+            P->info.tune_candidates = 0;
+            P->info.tune_cached = 1;
+            goto apply;
+        }
     }
-    float *dx = nullptr, *dg = nullptr;
-    double *df = nullptr;
-    CUDA_TRY(cudaMalloc(&dx, elems * sizeof(float)));
-    CUDA_TRY(cudaMalloc(&dg, elems * sizeof(float)));
-    CUDA_TRY(cudaMalloc(&df, (size_t)B * sizeof(double)));
-    CUDA_TRY(cudaMemcpy(dx, hx.data(), elems * sizeof(float), cudaMemcpyHostToDevice));
-    cudaEvent_t e0, e1;
-    CUDA_TRY(cudaEventCreate(&e0));
-    CUDA_TRY(cudaEventCreate(&e1));
-    float us[2] = {0.f, 0.f};
-    DevView cand[2] = {P->V32, view_for_image(P, V, 2)};
-    int nr[2] = {P->nr[0], P->nr[2]};
-    int mode[2];
-    size_t smem[2];
-    mode[0] = P->smem_mode32;
-    smem[0] = P->smem32;
-    mode[1] = smem_mode_for(P->n, sizeof(float), P->image[2].size() * sizeof(int4), P->max_smem, smem[1]);
-    FusedArgs a{};
-    a.B = B;
-    a.mode = MODE_EVAL;
-    a.x_in = dx;
-    a.f = df;
-    a.g = dg;
-    for (int c = 0; c < 2; ++c) {
-        CUDA_TRY(launcher_for(false, nr[c])(cand[c], mode[c], a, smem[c], 0, 0, true));
-        for (int w = 0; w < 2; ++w) CUDA_TRY(launcher_for(false, nr[c])(cand[c], mode[c], a, smem[c], B, 0, false));
-        CUDA_TRY(cudaEventRecord(e0, 0));
-        for (int r = 0; r < 5; ++r) CUDA_TRY(launcher_for(false, nr[c])(cand[c], mode[c], a, smem[c], B, 0, false));
-        CUDA_TRY(cudaEventRecord(e1, 0));
-        CUDA_TRY(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
-        us[c] = 1000.f * ms / 5.f;
+    {
+        const int B = 2 * P->num_sms;
+        const size_t elems = (size_t)B * (size_t)P->n;
+        std::vector<float> hx(elems);
+        uint64_t st = 0x9E3779B97F4A7C15ull;
+        for (size_t i = 0; i < elems; ++i) {
+            st = st * 6364136223846793005ull + 1442695040888963407ull;
+            hx[i] = (float)((double)(st >> 40) / (double)(1ull << 23) - 1.0);
+        }
+        float *dx = nullptr, *dg = nullptr;
+        double *df = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        int rc = FFSAT_OK;
+        int tried = 0;
+        auto cleanup = [&]() {
+            if (e0) cudaEventDestroy(e0);
+            if (e1) cudaEventDestroy(e1);
+            cudaFree(dx);
+            cudaFree(dg);
+            cudaFree(df);
+        };
+        // time the image currently in slot 0 with points-per-CTA pts
+        auto time_image = [&](int pts, float &us) -> int {
+            size_t smem = 0;
+            const int mode = smem_mode_for(P->n, sizeof(float), P->image[0].size() * sizeof(int4), P->max_smem, smem);
+            const DevView W = view_for_image(P, V, 0);
+            FusedArgs a{};
+            a.B = B;
+            a.mode = MODE_EVAL;
+            a.x_in = dx;
+            a.f = df;
+            a.g = dg;
+            const FusedFn fn = launcher_for(false, P->nr[0]);
+            const int grid = (B + pts - 1) / pts;
+            CUDA_TRY(fn(W, mode, a, smem, 0, 0, true));
+            CUDA_TRY(fn(W, mode, a, smem, grid, 0, false));
+            us = 1e30f;
+            for (int r = 0; r < 3; ++r) {
+                CUDA_TRY(cudaEventRecord(e0, 0));
+                CUDA_TRY(fn(W, mode, a, smem, grid, 0, false));
+                CUDA_TRY(cudaEventRecord(e1, 0));
+                CUDA_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                us = std::min(us, 1000.f * ms);
+            }
+            ++tried;
+            return FFSAT_OK;
+        };
+        // build, upload and time candidate (nr, kn); keep it as the best if faster
+        int best_nr = P->nr[0];
+        Knobs best = P->knobs[0];
+        float best_us = 0.f, default_us = 0.f;
+        std::vector<int4> best_tasks = P->tasks[0];
+        auto try_candidate = [&](int nr, const Knobs &kn) -> int {
+            P->nr[0] = nr;
+            P->knobs[0] = kn;
+            rebuild_image(P, 0);
+            if (P->tasks[0].size() == best_tasks.size() &&
+                std::memcmp(P->tasks[0].data(), best_tasks.data(), best_tasks.size() * sizeof(int4)) == 0 &&
+                kn.pts_per_cta == best.pts_per_cta)
+                return FFSAT_OK;  // the same image as the best so far
+            int r = check_image(P, 0);
+            if (r == FFSAT_OK) r = upload_image(P, 0);
+            float us = 0.f;
+            if (r == FFSAT_OK) r = time_image(kn.pts_per_cta, us);
+            if (r != FFSAT_OK) return r;
+            if (us < 0.99f * best_us) {
+                best_us = us;
+                best_nr = nr;
+                best = kn;
+                best_tasks = P->tasks[0];
+            }
+            return FFSAT_OK;
+        };
+        if (cudaMalloc(&dx, elems * sizeof(float)) != cudaSuccess || cudaMalloc(&dg, elems * sizeof(float)) != cudaSuccess ||
+            cudaMalloc(&df, (size_t)B * sizeof(double)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+            cudaEventCreate(&e1) != cudaSuccess ||
+            cudaMemcpy(dx, hx.data(), elems * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cleanup();
+            return fail(FFSAT_ERR_CUDA, "autotune: allocation or upload of the probe batch failed");
+        }
+        rc = time_image(best.pts_per_cta, default_us);
+        best_us = default_us;
+        // 1. node literals per lane
+        if (rc == FFSAT_OK && P->n_node_seg > 0 && P->opt.node_r == 0) {
+            for (int shape : {1, 2}) {
+                if (rc != FFSAT_OK) break;
+                Knobs kn = best;
+                kn.shape = shape;
+                rc = try_candidate(16, kn);
+            }
+            if (rc == FFSAT_OK && P->max_node_len <= 8 * 32) {
+                Knobs kn = best;
+                kn.shape = 0;
+                rc = try_candidate(8, kn);
+            }
+        }
+        // 2. clause groups per clause task
+        if (rc == FFSAT_OK && P->n_clause_pad + P->n_xor2_pad >= 64) {
+            for (int ck : {1, 2, 4}) {
+                if (rc != FFSAT_OK) break;
+                Knobs kn = best;
+                kn.clause_k = ck;
+                rc = try_candidate(best_nr, kn);
+            }
+        }
+        // 3. points per CTA
+        if (rc == FFSAT_OK) {
+            Knobs kn = best;
+            kn.pts_per_cta = 2;
+            rc = try_candidate(best_nr, kn);
+        }
+        cleanup();
+        if (rc != FFSAT_OK) return rc;
+        // slot 0 holds the last candidate: rebuild the best
+        P->nr[0] = best_nr;
+        P->knobs[0] = best;
+        rebuild_image(P, 0);
+        rc = check_image(P, 0);
+        if (rc == FFSAT_OK) rc = upload_image(P, 0);
+        if (rc != FFSAT_OK) return rc;
+        P->info.autotune_us[0] = default_us;
+        P->info.autotune_us[1] = best_us;
+        P->info.tune_candidates = tried;
+        P->info.tune_cached = 0;
+        std::lock_guard<std::mutex> lock(tune_mutex());
+        tune_cache()[key] = TuneChoice{best_nr, best, default_us, best_us, tried};
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(dx);
-    cudaFree(dg);
-    cudaFree(df);
+apply:
+    P->V32 = view_for_image(P, V, 0);
+    P->nr32 = P->nr[0];
+    P->smem_mode32 = smem_mode_for(P->n, sizeof(float), P->image[0].size() * sizeof(int4), P->max_smem, P->smem32);
+    CUDA_TRY(launcher_for(false, P->nr32)(P->V32, P->smem_mode32, FusedArgs{}, P->smem32, 0, 0, true));
     CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int32_t)));
-    if (us[1] < us[0]) {
-        std::swap(P->image[0], P->image[2]);
-        std::swap(P->tasks[0], P->tasks[2]);
-        std::swap(P->nr[0], P->nr[2]);
-        std::swap(P->off_image[0], P->off_image[2]);
-        for (int q = 0; q < 4; ++q) std::swap(P->img_off[0][q], P->img_off[2][q]);
-        P->V32 = view_for_image(P, V, 0);
-        P->nr32 = P->nr[0];
-        P->smem_mode32 = mode[1];
-        P->smem32 = smem[1];
-    }
     P->info.autotuned = 1;
-    P->info.autotune_us[0] = us[0];
-    P->info.autotune_us[1] = us[1];
     return FFSAT_OK;
 }
 
@@ -1137,32 +1319,14 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     }
     P->nr[0] = nr32;
     P->nr[1] = nr64;
-    TaskSet ts32, ts64;
-    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, nr32, fused_threads(false, nr32) / 32, node_imag, ts32);
-    build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, nr64, fused_threads(true, nr64) / 32, node_imag, ts64);
-    P->tasks[0] = ts32.tasks;
-    P->tasks[1] = ts64.tasks;
-    build_image(P, 0);
-    build_image(P, 1);
-    // autotune candidate: node R 8 against the default 16/12 family (FP32)
-    const bool tune = opt.autotune && !node_c.empty() && opt.node_r == 0 && max_node_len <= 8 * 32;
-    if (tune) {
-        TaskSet ts8;
-        build_tasks(seg_len, (int)node_c.size(), (int)n_clause_pad, (int)n_xor2_pad, 8, fused_threads(false, 8) / 32, node_imag, ts8);
-        P->n_images = 3;
-        P->nr[2] = 8;
-        P->tasks[2] = ts8.tasks;
-        build_image(P, 2);
-    }
-    // every literal the kernels will index must name a variable or one of the two dummies
-    for (int k = 0; k < P->n_images; ++k) {
-        const int32_t *w = reinterpret_cast<const int32_t *>(P->image[k].data());
-        for (size_t i = (size_t)P->img_off[k][1] * 4; i < (size_t)P->img_off[k][2] * 4; ++i)
-            if ((i & 3) != 3 && ((uint32_t)w[i] & 0x7fffffffu) > (uint32_t)n_vars + 1)
-                return fail(FFSAT_ERR_PARAM, "internal: clause record %zu out of range", i / 4);
-        for (size_t i = (size_t)P->img_off[k][3] * 4; i < P->image[k].size() * 4; ++i)
-            if (((uint32_t)w[i] & 0x7fffffffu) > (uint32_t)n_vars + 1)
-                return fail(FFSAT_ERR_PARAM, "internal: segment literal %zu out of range", i);
+    P->seg_len = seg_len;
+    P->n_clause_pad = (int)n_clause_pad;
+    P->n_xor2_pad = (int)n_xor2_pad;
+    P->max_node_len = max_node_len;
+    for (int k = 0; k < 2; ++k) {
+        rebuild_image(P, k);
+        rc = check_image(P, k);
+        if (rc != FFSAT_OK) return rc;
     }
 
     // ---- device ----
@@ -1175,7 +1339,6 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     CUDA_TRY(cudaDeviceGetAttribute(&P->max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
 
     Arena A;
-    for (int k = 0; k < P->n_images; ++k) P->off_image[k] = A.put(P->image[k]);
     P->off_clause_wd = A.put(P->clause_wd);
     P->off_seg_wd = A.put(P->seg_wd);
     const size_t o_tf = A.put(tab_f), o_td = A.put(tab_d);
@@ -1215,6 +1378,10 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     CUDA_TRY(cudaMemcpy(P->d_arena, A.host.data(), P->arena_bytes, cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMalloc(&P->d_status, sizeof(int32_t)));
     CUDA_TRY(cudaMemset(P->d_status, 0, sizeof(int32_t)));
+    for (int k = 0; k < 2; ++k) {
+        rc = upload_image(P, k);
+        if (rc != FFSAT_OK) return rc;
+    }
 
     unsigned char *base = P->d_arena;
     DevView V{};
@@ -1256,7 +1423,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     FusedArgs dummy{};
     CUDA_TRY(launcher_for(false, nr32)(P->V32, P->smem_mode32, dummy, P->smem32, 0, 0, true));
     CUDA_TRY(launcher_for(true, nr64)(P->V64, P->smem_mode64, dummy, P->smem64, 0, 0, true));
-    if (tune) {
+    if (opt.autotune) {
         rc = autotune(P, V);
         if (rc != FFSAT_OK) return rc;
         nr32 = P->nr32;
@@ -1276,6 +1443,9 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     inf.n_tables = (int32_t)tab_index.size();
     inf.n_tasks = (int32_t)P->tasks[0].size();
     inf.node_r = nr32;
+    inf.tune_shape = P->knobs[0].shape;
+    inf.tune_clause_k = P->knobs[0].clause_k;
+    inf.tune_pts_per_cta = P->knobs[0].pts_per_cta;
     inf.smem_mode_f32 = P->smem_mode32;
     inf.smem_mode_f64 = P->smem_mode64;
     inf.threads_f32 = fused_threads(false, nr32);
@@ -1300,8 +1470,8 @@ int ffsat_set_weights(ffsat_instance *I, const double *weights) {
     CUDA_TRY(dev_guard.set(I->device));
     unsigned char *base = I->d_arena;
     for (int k = 0; k < I->n_images; ++k) {
-        build_image(I, k);
-        CUDA_TRY(cudaMemcpy(base + I->off_image[k], I->image[k].data(), I->image[k].size() * sizeof(int4), cudaMemcpyHostToDevice));
+        build_image(I, k);  // same tasks and tile choices: the same size
+        CUDA_TRY(cudaMemcpy(I->d_img[k], I->image[k].data(), I->image[k].size() * sizeof(int4), cudaMemcpyHostToDevice));
     }
     CUDA_TRY(cudaMemcpy(base + I->off_clause_wd, I->clause_wd.data(), I->clause_wd.size() * sizeof(double), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(base + I->off_seg_wd, I->seg_wd.data(), I->seg_wd.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -1322,7 +1492,12 @@ static int check_dtype(int32_t dtype) {
     return FFSAT_OK;
 }
 
-static inline int grid_for(int32_t B) { return B; }
+// CTAs of a fused-kernel launch on B points: each CTA runs pts_per_cta points in
+// turn (the image's tile choice; one by default).
+static inline int grid_for(const ffsat_instance *I, bool f64, int32_t B) {
+    const int k = std::max(1, I->knobs[f64 ? 1 : 0].pts_per_cta);
+    return (B + k - 1) / k;
+}
 
 using ClusterFn = cudaError_t (*)(const DevView &, int, const FusedArgs &, size_t, size_t, int, int, cudaStream_t,
                                   int *);
@@ -1373,7 +1548,7 @@ static int launch_step(ffsat_instance *I, bool f64, int mode, const FusedArgs &a
         CUDA_TRY(cluster_launcher(I->nr64)(V, mode, a, csmem, g1_off, B, cl, static_cast<cudaStream_t>(stream),
                                            nullptr));
     else
-        CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(B),
+        CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(I, f64, B),
                                                               static_cast<cudaStream_t>(stream), false));
     t_cluster = cl;
     t_launches = 1;
@@ -1402,7 +1577,7 @@ int ffsat_eval_grad(ffsat_instance *I, int32_t B, const void *x, int32_t dtype, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const DevView &V = f64 ? I->V64 : I->V32;
     CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, f64 ? I->smem_mode64 : I->smem_mode32, a,
-                                                          f64 ? I->smem64 : I->smem32, grid_for(B), s, false));
+                                                          f64 ? I->smem64 : I->smem32, grid_for(I, f64, B), s, false));
     t_launches = 1;
     return FFSAT_OK;
 }
@@ -1575,7 +1750,7 @@ int ffsat_step_pgfp(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const 
     if (rc) return rc;
     a.y_scratch = I->d_yscratch;
     const DevView &V = f64 ? I->V64 : I->V32;
-    CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(B),
+    CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(I, f64, B),
                                                           static_cast<cudaStream_t>(stream), false));
     t_launches = 1;
     return FFSAT_OK;
@@ -1631,7 +1806,7 @@ int ffsat_erwa_update(ffsat_instance *I, const int32_t *U, double alpha, void *s
     W.m = I->m;
     W.n_images = I->n_images;
     for (int k = 0; k < I->n_images; ++k) {
-        int4 *img = reinterpret_cast<int4 *>(base + I->off_image[k]);
+        int4 *img = I->d_img[k];
         W.clauses[k] = img + I->img_off[k][1];
         W.segmeta[k] = img + I->img_off[k][2];
     }
@@ -1790,6 +1965,8 @@ struct ffsat_batch {
     int num_sms = 0;
     std::vector<ffsat_instance *> insts;
     int node_r[2] = {0, 0};      // batch-kernel variant per real type (0 or 16)
+    int threads[2] = {0, 0};     // CTA width per real type
+    float tune_us[2] = {0.f, 0.f};  // FP32 probe evaluation at 384 / 512 threads (0: not timed)
     size_t smem[2] = {0, 0};
     int grid[2] = {0, 0};
     std::vector<BatchInst> h_insts;  // last table uploaded (per real type: re-uploaded when it changes)
@@ -1912,10 +2089,81 @@ int batch_launch(ffsat_batch *bt, const ffsat_batch_io *io, int32_t dtype, int m
     }
     CUDA_TRY(cudaMemsetAsync(bt->d_counter, 0, sizeof(int), s));
     const int v = f64 ? 1 : 0;
-    CUDA_TRY(launch_batch(f64, bt->node_r[v], bt->d_insts, bt->d_items, bt->n_items, bt->d_counter, sp, bt->smem[v],
+    CUDA_TRY(launch_batch(f64, bt->node_r[v], bt->threads[v], bt->d_insts, bt->d_items, bt->n_items, bt->d_counter, sp, bt->smem[v],
                           bt->grid[v], s, false, nullptr));
     t_launches = 1;
     return FFSAT_OK;
+}
+
+
+// CTA width `threads` for real type v, and the persistent grid it allows.
+int batch_set_threads(ffsat_batch *bt, int v, int threads) {
+    int per_sm = 0;
+    const StepParams none{};
+    CUDA_TRY(launch_batch(v == 1, bt->node_r[v], threads, nullptr, nullptr, 0, nullptr, none, bt->smem[v], 0, 0, true,
+                          &per_sm));
+    bt->threads[v] = threads;
+    bt->grid[v] = std::max(1, per_sm) * bt->num_sms;
+    return FFSAT_OK;
+}
+
+// Time one FP32 batch evaluation (two points per instance, min over three
+// launches after a warm-up) at 384 and at 512 threads per CTA and keep the
+// faster width (512 unless 384 is at least 1% faster).
+int batch_tune_threads(ffsat_batch *bt) {
+    const int K = (int)bt->insts.size();
+    const int P = 2;
+    size_t xs = 0;
+    for (ffsat_instance *I : bt->insts) xs += (size_t)P * (size_t)I->n;
+    std::vector<float> hx(xs);
+    uint64_t st = 0xD1B54A32D192ED03ull;
+    for (size_t i = 0; i < xs; ++i) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        hx[i] = (float)((double)(st >> 40) / (double)(1ull << 23) - 1.0);
+    }
+    float *dx = nullptr, *dg = nullptr;
+    double *df = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = FFSAT_OK;
+    if (cudaMalloc(&dx, xs * sizeof(float)) != cudaSuccess || cudaMalloc(&dg, xs * sizeof(float)) != cudaSuccess ||
+        cudaMalloc(&df, (size_t)K * P * sizeof(double)) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess ||
+        cudaMemcpy(dx, hx.data(), xs * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+        rc = fail(FFSAT_ERR_CUDA, "batch tuning: allocation or upload of the probe batch failed");
+    std::vector<ffsat_batch_io> io(K);
+    size_t off = 0;
+    for (int k = 0; k < K; ++k) {
+        std::memset(&io[k], 0, sizeof(io[k]));
+        io[k].B = P;
+        io[k].x = dx + off;
+        io[k].g = dg + off;
+        io[k].f = df + (size_t)k * P;
+        off += (size_t)P * (size_t)bt->insts[k]->n;
+    }
+    const int widths[2] = {384, 512};
+    for (int c = 0; c < 2 && rc == FFSAT_OK; ++c) {
+        rc = batch_set_threads(bt, 0, widths[c]);
+        if (rc == FFSAT_OK) rc = batch_launch(bt, io.data(), FFSAT_F32, MODE_EVAL, nullptr, 0);
+        float best = 1e30f;
+        for (int r = 0; r < 3 && rc == FFSAT_OK; ++r) {
+            float ms = 0.f;
+            if (cudaEventRecord(e0, 0) != cudaSuccess) rc = fail(FFSAT_ERR_CUDA, "batch tuning: event record failed");
+            if (rc == FFSAT_OK) rc = batch_launch(bt, io.data(), FFSAT_F32, MODE_EVAL, nullptr, 0);
+            if (rc == FFSAT_OK && (cudaEventRecord(e1, 0) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                                   cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+                rc = fail(FFSAT_ERR_CUDA, "batch tuning: timing failed");
+            best = std::min(best, 1000.f * ms);
+        }
+        bt->tune_us[c] = best;
+    }
+    if (rc == FFSAT_OK) rc = batch_set_threads(bt, 0, bt->tune_us[0] < 0.99f * bt->tune_us[1] ? 384 : 512);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaFree(dx);
+    cudaFree(dg);
+    cudaFree(df);
+    for (ffsat_instance *I : bt->insts) cudaMemset(I->d_status, 0, sizeof(int32_t));
+    return rc;
 }
 
 }  // namespace
@@ -1945,14 +2193,31 @@ int ffsat_batch_create(ffsat_instance *const *insts, int32_t count, ffsat_batch 
         }
         bt->smem[v] = smem;
         bt->node_r[v] = nr;
-        int per_sm = 0;
-        const StepParams none{};
-        CUDA_TRY(launch_batch(v == 1, nr, nullptr, nullptr, 0, nullptr, none, smem, 0, 0, true, &per_sm));
-        bt->grid[v] = std::max(1, per_sm) * bt->num_sms;
+        int rc = batch_set_threads(bt.get(), v, batch_threads_default(v == 1, nr));
+        if (rc != FFSAT_OK) return rc;
     }
     CUDA_TRY(cudaMalloc(&bt->d_insts, (size_t)count * sizeof(BatchInst)));
     CUDA_TRY(cudaMalloc(&bt->d_counter, sizeof(int)));
+    // FP32 node-path batches of autotuned instances also choose the CTA width
+    bool tuned = bt->node_r[0] > 0;
+    for (ffsat_instance *I : bt->insts) tuned = tuned && I->opt.autotune;
+    if (tuned) {
+        int rc = batch_tune_threads(bt.get());
+        if (rc != FFSAT_OK) return rc;
+    }
     *out = bt.release();
+    return FFSAT_OK;
+}
+
+int ffsat_batch_threads(const ffsat_batch *bt, int32_t dtype, int32_t *threads, float *us384, float *us512) {
+    t_err.clear();
+    if (!bt || !threads) return fail(FFSAT_ERR_ARG, "NULL argument");
+    int rc = check_dtype(dtype);
+    if (rc) return rc;
+    const int v = dtype == FFSAT_F64 ? 1 : 0;
+    *threads = bt->threads[v];
+    if (us384) *us384 = v == 0 ? bt->tune_us[0] : 0.f;
+    if (us512) *us512 = v == 0 ? bt->tune_us[1] : 0.f;
     return FFSAT_OK;
 }
 
@@ -2017,6 +2282,8 @@ void ffsat_free(ffsat_instance *I) {
     DeviceGuard dev_guard;
     dev_guard.set(I->device);
     if (I->d_graph) cudaFree(I->d_graph);
+    for (int k = 0; k < 2; ++k)
+        if (I->d_img[k]) cudaFree(I->d_img[k]);
     if (I->d_arena) cudaFree(I->d_arena);
     if (I->d_status) cudaFree(I->d_status);
     if (I->d_scratch) cudaFree(I->d_scratch);

@@ -130,11 +130,9 @@ constexpr int fused_threads(bool f64, int node_r) {
     return f64 ? (node_r >= 16 ? 128 : 256) : (node_r >= 16 ? 512 : (node_r > 0 ? 512 : 1024));
 }
 
-// Threads per CTA of the batch kernel: as the fused kernel, but 384 for the FP32
-// node path (node factors kept in registers, see run_point).
-constexpr int batch_threads_for(bool f64, int node_r) {
-    return (!f64 && node_r >= 16) ? 384 : fused_threads(f64, node_r);
-}
+// Threads per CTA of the batch kernel: as the fused kernel; FP32 node-path
+// batches also have a 384-thread instance (ffsat_batch_create may pick it).
+constexpr int batch_threads_default(bool f64, int node_r) { return fused_threads(f64, node_r); }
 
 // Mode of the fused kernel.
 enum : int32_t { MODE_EVAL = 0, MODE_STEP = 1, MODE_PGFP = 2 };
@@ -171,13 +169,21 @@ struct BatchInst {
     int32_t pad[3];
 };
 
-// Batch-kernel launchers (f64: real type; node_r: 0 or 16).  With prepare_only
-// the launcher raises the dynamic shared-memory limit to `smem` and reports
-// through *blocks_per_sm how many CTAs of the kernel fit on one SM.
-cudaError_t launch_batch(bool f64, int node_r, const BatchInst *insts, const int2 *items, int n_items, int *counter,
-                         const StepParams &sp, size_t smem, int grid, cudaStream_t s, bool prepare_only,
+// Batch-kernel launchers (f64: real type; node_r: 0 or 16; threads: the CTA
+// width, 384 or 512 for FP32 with node_r 16, ignored otherwise).  With
+// prepare_only the launcher raises the dynamic shared-memory limit to `smem` and
+// reports through *blocks_per_sm how many CTAs of the kernel fit on one SM.
+cudaError_t launch_batch(bool f64, int node_r, int threads, const BatchInst *insts, const int2 *items, int n_items,
+                         int *counter, const StepParams &sp, size_t smem, int grid, cudaStream_t s, bool prepare_only,
                          int *blocks_per_sm);
-int batch_threads(bool f64, int node_r);
+#define FFSAT_BATCH_LAUNCHER(name)                                                                       \
+    cudaError_t name(const BatchInst *insts, const int2 *items, int n_items, int *counter, const StepParams &sp, \
+                     size_t smem, int grid, cudaStream_t s, bool prepare_only, int *blocks_per_sm)
+FFSAT_BATCH_LAUNCHER(batch_f32_r16_t384);
+FFSAT_BATCH_LAUNCHER(batch_f32_r16_t512);
+FFSAT_BATCH_LAUNCHER(batch_f32_r0);
+FFSAT_BATCH_LAUNCHER(batch_f64_r16);
+FFSAT_BATCH_LAUNCHER(batch_f64_r0);
 
 // Fused-kernel launchers, one per (real type, node R); each handles the three
 // shared-memory modes.  With prepare_only the launcher only raises the kernel's

@@ -57,6 +57,7 @@ SYMBOLS = (
     "ffsat_batch_create",
     "ffsat_batch_eval_grad",
     "ffsat_batch_step",
+    "ffsat_batch_threads",
     "ffsat_batch_free",
     "ffsat_mpnn_create",
     "ffsat_mpnn_num_params",
@@ -135,7 +136,9 @@ class Info(C.Structure):
                 ("smem_mode_f64", C.c_int32), ("threads_f32", C.c_int32), ("node_lane_work", C.c_int64),
                 ("device_bytes", C.c_int64), ("autotuned", C.c_int32), ("autotune_us", C.c_float * 2),
                 ("n_xor2", C.c_int32), ("pad", C.c_int32), ("smem_bytes_f32", C.c_int64),
-                ("smem_bytes_f64", C.c_int64)]
+                ("smem_bytes_f64", C.c_int64), ("tune_shape", C.c_int32), ("tune_clause_k", C.c_int32),
+                ("tune_pts_per_cta", C.c_int32), ("tune_candidates", C.c_int32), ("tune_cached", C.c_int32),
+                ("pad2", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}
@@ -193,6 +196,9 @@ def lib():
         L.ffsat_batch_eval_grad.restype = C.c_int
         L.ffsat_batch_step.argtypes = [_vp, C.POINTER(BatchIO), C.c_int32, C.POINTER(StepArgs), _vp]
         L.ffsat_batch_step.restype = C.c_int
+        L.ffsat_batch_threads.argtypes = [_vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_float),
+                                          C.POINTER(C.c_float)]
+        L.ffsat_batch_threads.restype = C.c_int
         L.ffsat_batch_free.argtypes = [_vp]
         L.ffsat_batch_free.restype = None
         L.ffsat_mpnn_create.argtypes = [C.c_int32, C.c_uint64, C.POINTER(_vp)]
@@ -516,6 +522,12 @@ class Batch:
             self.free()
         except Exception:
             pass
+
+    def threads(self, dtype: int = FFSAT_F32):
+        """(threads per CTA of the batch kernel, FP32 probe times at 384 and 512 threads in us)."""
+        th, a, b = C.c_int32(0), C.c_float(0.0), C.c_float(0.0)
+        _check(lib().ffsat_batch_threads(self.handle, int(dtype), C.byref(th), C.byref(a), C.byref(b)))
+        return th.value, a.value, b.value
 
     def _io(self, xs, fs=None, gs=None, solved=None, n_unsat=None, b_offsets=None):
         io = (BatchIO * len(self.instances))()

@@ -86,6 +86,10 @@ def test_uneven_batch_shape_sampled():
 
 
 def test_autotune_picks_a_candidate_and_stays_exact():
+    """The load-time autotuner times candidate tile choices (node literals per
+    lane and segment shape, clause groups per task, points per CTA), keeps the
+    fastest, reuses the choice for an instance of the same shape, and the tuned
+    image evaluates and steps within the oracle's tolerance."""
     from paper_2308_15020_gb300 import ffsat
 
     inst = gen.concat([gen.random_ksat(3000, 9000, 3, 7), gen.random_atleast(3000, 60, 16, 200, 7)])
@@ -93,6 +97,10 @@ def test_autotune_picks_a_candidate_and_stays_exact():
     info = h.info()
     assert info["autotuned"] == 1 and info["node_r"] in (8, 16)
     assert all(t > 0 for t in info["autotune_us"])
+    assert info["autotune_us"][1] <= info["autotune_us"][0]
+    assert info["tune_cached"] == 0 and info["tune_candidates"] >= 4
+    assert info["tune_shape"] in (0, 1, 2) and info["tune_clause_k"] in (0, 1, 2, 4)
+    assert info["tune_pts_per_cta"] in (1, 2)
     x = gen.uniform_points(9, inst.n, 3)
     f, g = h.eval_grad(torch.from_numpy(x).cuda())
     ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4)
@@ -102,6 +110,35 @@ def test_autotune_picks_a_candidate_and_stays_exact():
     f, g = h.eval_grad(torch.from_numpy(x).cuda())
     ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4, weights=w)
     assert ef <= 1 and eg <= 1
+    # an instance of another seed (its own shape, or a cached one) steps within tolerance
+    inst2 = gen.concat([gen.random_ksat(3000, 9000, 3, 8), gen.random_atleast(3000, 60, 16, 200, 8)])
+    h2 = ffsat.Instance(inst2, autotune=True)
+    assert h2.info()["autotuned"] == 1
+    x2 = gen.uniform_points(5, inst2.n, 4)
+    xt = torch.from_numpy(x2).cuda()
+    solved, nun = h2.step(xt, T=1, lr=0.05, seed=1, restart=False)
+    _, gs = O.eval_grad(inst2, x2.astype(np.float64))
+    _, A = O.eval_scale(inst2, x2.astype(np.float64), 1e-2)
+    tol = 0.05 * 1e-4 * np.maximum(np.abs(gs), A) + 1e-7
+    assert np.all(np.abs(to_np(xt) - np.clip(x2 - 0.05 * gs, -1, 1)) <= tol)
+    # the same instance loaded again hits the cache
+    h3 = ffsat.Instance(inst, autotune=True)
+    i3 = h3.info()
+    assert i3["tune_cached"] == 1 and i3["tune_candidates"] == 0
+    assert (i3["node_r"], i3["tune_shape"], i3["tune_clause_k"], i3["tune_pts_per_cta"]) == \
+        (info["node_r"], info["tune_shape"], info["tune_clause_k"], info["tune_pts_per_cta"])
+    f3, g3 = h3.eval_grad(torch.from_numpy(x).cuda())
+    h3.set_weights(np.ones(inst.m))
+    # a batch of autotuned instances times both CTA widths of its FP32 kernel
+    bt = ffsat.Batch([h, h3])
+    th, us384, us512 = bt.threads()
+    assert th in (384, 512) and us384 > 0 and us512 > 0
+    assert ffsat.Batch([ffsat.Instance(inst)]).threads()[0] == 512
+    fs, gs = bt.eval_grad([torch.from_numpy(x).cuda(), torch.from_numpy(x).cuda()])
+    ef, eg = compare(inst, x, to_np(fs[1]), to_np(gs[1]), 1e-4)
+    assert ef <= 1 and eg <= 1
+    for hh in (h, h2, h3):
+        hh.sync_status()
 
 
 def test_batch_step_replays_from_a_cuda_graph():
