@@ -191,6 +191,8 @@ class SatRun:
     best_unsat: int = -1  # fewest violated constraints of any point seen (0 when solved)
     # (seconds since the start, fewest violated constraints so far) after every round
     trajectory: List[Tuple[float, int]] = field(default_factory=list)
+    # violated constraints of the best point, by type (with keep_best)
+    violated_by_type: Optional[dict] = None
 
     def time_to_unsat(self, k: int) -> float:
         """Seconds until some point violated at most k constraints (inf if never)."""
@@ -198,10 +200,13 @@ class SatRun:
 
 
 def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optional[ffsat.MPNN] = None,
-                target_unsat: int = 0) -> SatRun:
+                target_unsat: int = 0, keep_best: bool = False, ctype=None) -> SatRun:
     """Wall time until some point's sign vector is a model (Alg. 1) -- or violates
     at most target_unsat constraints -- with uniform restarts (net None) or
-    restarts drawn around the network's proposal."""
+    restarts drawn around the network's proposal.  With keep_best (and the
+    instance's constraint types `ctype`) the best point is kept on the device
+    (no extra host synchronisation) and the constraints it violates are counted
+    by type after the run."""
     import torch
 
     if cfg.heuristics:
@@ -212,15 +217,36 @@ def time_to_sat(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, net: Optio
     S = CLSSearch(h, n, cfg, seed, prop)
     best = None
     traj = []
+    keep = {}
+
+    def on_checked(x, solved, nun):
+        i = nun.argmin()
+        u, row = nun[i], x[i]
+        if "x" not in keep:
+            keep["u"], keep["x"] = u.clone(), row.clone()
+        else:
+            better = u < keep["u"]
+            keep["x"] = torch.where(better, row, keep["x"])
+            keep["u"] = torch.minimum(keep["u"], u)
+
+    run = None
     for r in range(cfg.max_rounds):
-        solved, nun = S.round(r)
+        solved, nun = S.round(r, on_checked if keep_best else None)
         m = nun.min()
         best = m if best is None else torch.minimum(best, m)
         b = int(best.item())  # the round's one host synchronisation
         traj.append((time.perf_counter() - t0, b))
         if b <= target_unsat:
-            return SatRun(True, traj[-1][0], r + 1, 0, traj)
-    return SatRun(False, time.perf_counter() - t0, cfg.max_rounds, traj[-1][1] if traj else -1, traj)
+            run = SatRun(True, traj[-1][0], r + 1, 0, traj)
+            break
+    if run is None:
+        run = SatRun(False, time.perf_counter() - t0, cfg.max_rounds, traj[-1][1] if traj else -1, traj)
+    if keep_best and "x" in keep and ctype is not None:
+        U = h.unsat_counts(keep["x"].reshape(1, -1).contiguous()).cpu().numpy()
+        ct = np.asarray(ctype)
+        run.violated_by_type = {name: int(U[ct == t].sum()) for name, t in
+                                (("clauses", ffsat.FFSAT_OR), ("xor", ffsat.FFSAT_XOR), ("atleast", ffsat.FFSAT_ATLEAST))}
+    return run
 
 
 def time_to_sat_graph(h: ffsat.Instance, n: int, cfg: CLSConfig, seed: int, target_unsat: int = 0,
@@ -312,7 +338,16 @@ class ABResult:
             # fixed ladder of K: time-to-SAT is the K = 0 rung
             "median_par2_s_to_unsat_le": {
                 str(K): {k: self._par2_to(v, K, budget) for k, v in arms.items()} for K in UNSAT_LADDER},
+            # mean violated constraints of each run's best point, by type
+            "violated_at_best_by_type": {k: self._by_type(v) for k, v in arms.items()},
         }
+
+    @staticmethod
+    def _by_type(runs):
+        rs = [r.violated_by_type for r in runs if r.violated_by_type is not None]
+        if not rs:
+            return None
+        return {t: float(np.mean([r[t] for r in rs])) for t in rs[0]}
 
     @staticmethod
     def _par2_to(runs, K, budget):
@@ -341,8 +376,8 @@ def ab_test(net: ffsat.MPNN, instances, cfg: CLSConfig) -> ABResult:
         h = ffsat.Instance(inst)
         seed = cfg.seed + 7919 * k
         warm(h, inst.n, cfg, net)
-        res.uniform.append(time_to_sat(h, inst.n, cfg, seed, None))
-        res.learned.append(time_to_sat(h, inst.n, cfg, seed, net))
+        res.uniform.append(time_to_sat(h, inst.n, cfg, seed, None, keep_best=True, ctype=inst.ctype))
+        res.learned.append(time_to_sat(h, inst.n, cfg, seed, net, keep_best=True, ctype=inst.ctype))
     return res
 
 
