@@ -58,21 +58,28 @@ __device__ __forceinline__ double ld_peer(const double *local, int v, int rank) 
 }
 
 // The warp tasks t with t mod CL = rank, pulled in order from the CTA's counter;
-// gradient contributions go to G.  Starts and ends with a CTA barrier.
+// gradient contributions go to G.  The counter is never reset: every warp pulls
+// until its first pull past this CTA's n_local tasks, so an iteration makes
+// exactly n_local + (warps per CTA) pulls and iteration `it` owns the pulls from
+// it * (n_local + warps) on.  The caller separates iterations by barriers (the
+// cluster barrier after the evaluation, a CTA barrier after the update) and
+// zeroes the counter before the first.
 template <typename R, int NR, int NI, int XG, typename Acc>
 __device__ __forceinline__ void eval_tasks_strided(const DevView &V, const Src &S, const R *xrow, const Acc &G,
-                                                   int &s_ctr, int rank, int CL) {
+                                                   int &s_ctr, int rank, int CL, int it) {
     constexpr bool SF = false;  // FP64 node factors are recomputed in the prefix pass
     const int lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) s_ctr = 0;
-    __syncthreads();
+    const int n_local = (V.n_task - rank + CL - 1) / CL;
+    // unsigned: the counter and the base wrap together for any T
+    const unsigned base = (unsigned)it * (unsigned)(n_local + (int)(blockDim.x >> 5));
     R facc = R(0);  // the objective is not needed by a fixed-step call
     for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(&s_ctr, 1);
-        t = __shfl_sync(kFull, t, 0) * CL + rank;
-        if (t >= V.n_task) break;
-        const int4 task = S.tasks[t];
+        unsigned t = 0;
+        if (lane == 0) t = atomicAdd(reinterpret_cast<unsigned *>(&s_ctr), 1u);
+        const int tl = (int)(__shfl_sync(kFull, t, 0) - base);
+        if (tl >= n_local) break;
+        const int tg = tl * CL + rank;
+        const int4 task = S.tasks[tg];
         const int kind = task.x & 0xff;
         const bool xr = kind == TASK_XOR2;
         if (kind == TASK_CLAUSE || xr) {
@@ -92,7 +99,6 @@ __device__ __forceinline__ void eval_tasks_strided(const DevView &V, const Src &
             node_dispatch<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
         }
     }
-    __syncthreads();
 }
 
 // Shared memory: x | gradient buffer 0 | resident image (SMEM_RES) as in the
@@ -130,14 +136,16 @@ __global__ void __launch_bounds__(THREADS, 1) fused_cluster_kernel(const DevView
         g0[v] = R(0);
         g1[v] = R(0);
     }
+    if (tid == 0) sh.ctr = 0;
+    __syncthreads();
     const R lr = R(A.sp.lr);
     for (int it = 0; it < A.sp.T; ++it) {
         R *const gw = (it & 1) ? g1 : g0;
         R *const gz = (it & 1) ? g0 : g1;
         PlainAcc<R> G;
         G.g = gw;
-        eval_tasks_strided<R, NR, NI, SMEM_FULL>(V, S, xs, G, sh.ctr, rank, CL);
-        cluster_barrier();
+        eval_tasks_strided<R, NR, NI, SMEM_FULL>(V, S, xs, G, sh.ctr, rank, CL, it);
+        cluster_barrier();  // also ends the evaluation of this CTA's warps
         for (int v = tid; v < n; v += THREADS) {
             R g = R(0);
             for (int q = 0; q < CL; ++q) g += ld_peer(gw, v, q);
@@ -146,7 +154,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_cluster_kernel(const DevView
             xs[v] = z;
             gz[v] = R(0);
         }
-        // the next evaluation starts with a CTA barrier
+        __syncthreads();  // x and the cleared buffer before the next evaluation
     }
     cluster_barrier();  // no peer reads this CTA's buffers after this point
     if (rank != 0) return;

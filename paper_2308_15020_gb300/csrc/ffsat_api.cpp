@@ -1319,6 +1319,10 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     }
     P->nr[0] = nr32;
     P->nr[1] = nr64;
+    // FP64 steps on few points spread each point over a cluster of CTAs that
+    // split the warp tasks: one clause group of 32 per task keeps every warp of
+    // the cluster busy with a short task
+    P->knobs[1].clause_k = 1;
     P->seg_len = seg_len;
     P->n_clause_pad = (int)n_clause_pad;
     P->n_xor2_pad = (int)n_xor2_pad;
