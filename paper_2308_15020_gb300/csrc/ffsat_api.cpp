@@ -248,7 +248,8 @@ inline int32_t pack_lit(int32_t l) {
 inline int seg_lanes(int L, int R) { return std::max(1, pow2_at_least((L + R - 1) / R)); }
 
 // Literals per lane of a node segment.  A kernel built for node R = 16 also
-// runs 12 and 8 literals per lane; per segment the host picks the shape with
+// runs 12 and 8 literals per lane, and in FP32 with the imaginary-node form 14
+// and 10 (read as 8-byte pairs); per segment the host picks the shape with
 // the smallest modelled issue cost per node, G * (7 NR + 58 + 8 log2 G) lane
 // instructions for the imaginary-node task (7 per literal slot; per node the
 // normalisation, division and scales, and per butterfly level three shuffles,
@@ -257,7 +258,7 @@ inline int seg_lanes(int L, int R) { return std::max(1, pow2_at_least((L + R - 1
 // The autotuner may replace the model by another segment shape: the fewest
 // lanes per segment (shape 1; ties to fewer literal slots) or the fewest literal
 // slots G * NR (shape 2; ties to fewer lanes).
-inline int node_nr(int L, int nr_max, bool imag, int shape = 0) {
+inline int node_nr(int L, int nr_max, bool imag, int shape = 0, bool f32 = true) {
     if (nr_max < 16) return nr_max;
     auto cost = [&](int nr) {
         const int G = seg_lanes(L, nr);
@@ -268,8 +269,11 @@ inline int node_nr(int L, int nr_max, bool imag, int shape = 0) {
         return imag ? (double)G * (7.0 * nr + 58.0 + 8.0 * lg) : (double)G * (14.0 * nr + 12.0 + 10.0 * lg);
     };
     int best = 16;
-    for (int nr : {12, 8})
+    for (int nr : {14, 12, 10, 8}) {
+        // the generic node task, and the FP64 kernels, run 16, 12 and 8
+        if ((nr == 14 || nr == 10) && !(imag && f32)) continue;
         if (cost(nr) < cost(best)) best = nr;
+    }
     return best;
 }
 
@@ -446,7 +450,7 @@ int clause_groups_per_task(int groups, int other_tasks, int warps) {
 }
 
 void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clause, int n_xor2, int node_r,
-                 int warps, bool imag, const Knobs &kn, TaskSet &ts) {
+                 int warps, bool imag, const Knobs &kn, TaskSet &ts, bool f32) {
     ts.tasks.clear();
     ts.node_r = node_r;
     auto group = [&](int first, int count, int kind, int R) {
@@ -454,13 +458,13 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
         const int end = first + count;
         while (i < end) {
             const int L = seg_len[i];
-            const int nr = kind == TASK_NODE ? node_nr(L, R, imag, kn.shape) : R;
+            const int nr = kind == TASK_NODE ? node_nr(L, R, imag, kn.shape, f32) : R;
             const int G = seg_lanes(L, nr);
             const int S = 32 / G;
             int k = 0;
             while (k < S && i + k < end) {
                 const int Lk = seg_len[i + k];
-                const int nk = kind == TASK_NODE ? node_nr(Lk, R, imag, kn.shape) : R;
+                const int nk = kind == TASK_NODE ? node_nr(Lk, R, imag, kn.shape, f32) : R;
                 if (nk != nr || seg_lanes(Lk, nk) != G) break;
                 ++k;
             }
@@ -716,12 +720,14 @@ void build_image(ffsat_instance *I, int k) {
     for (size_t s = 0; s < I->seg_info.size(); ++s) {
         const int4 si = I->seg_info[s];
         const bool node = (int)s < I->n_node_seg;
-        const int R = node ? node_nr(si.y, nr, I->opt.form == FFSAT_FORM_STABLE, I->knobs[k].shape) : kProdR;
+        const int R = node ? node_nr(si.y, nr, I->opt.form == FFSAT_FORM_STABLE, I->knobs[k].shape, k == 0) : kProdR;
         const int G = seg_lanes(si.y, R);
         const int32_t pad = node ? I->pad_node : I->n;
         const int32_t off = (int32_t)lits.size();
         lits.insert(lits.end(), I->seg_lits.begin() + si.x, I->seg_lits.begin() + si.x + si.y);
-        lits.resize((size_t)off + (size_t)G * R, pad);
+        // every segment starts on a 16-byte boundary (lanes of 10 or 14 literals
+        // leave odd pairs at the end of one-lane segments)
+        lits.resize(((size_t)off + (size_t)G * R + 3) & ~size_t(3), pad);
         meta[s] = make_int4(off, si.y, si.z, si.w);
     }
     for (const int4 &t : I->tasks[k])
@@ -900,7 +906,7 @@ DevView view_for_image(ffsat_instance *P, const DevView &V, int k) {
 void rebuild_image(ffsat_instance *P, int k) {
     TaskSet ts;
     build_tasks(P->seg_len, P->n_node_seg, P->n_clause_pad, P->n_xor2_pad, P->nr[k],
-                fused_threads(k == 1, P->nr[k]) / 32, P->opt.form == FFSAT_FORM_STABLE, P->knobs[k], ts);
+                fused_threads(k == 1, P->nr[k]) / 32, P->opt.form == FFSAT_FORM_STABLE, P->knobs[k], ts, k == 0);
     P->tasks[k] = ts.tasks;
     build_image(P, k);
 }

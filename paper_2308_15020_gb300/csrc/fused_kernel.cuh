@@ -140,7 +140,13 @@ __device__ __forceinline__ void prefetch_node_im(const DevView &V, float, int id
 __device__ __forceinline__ void prefetch_node_im(const DevView &V, double, int idx) {
     asm volatile("prefetch.global.L1 [%0];" ::"l"(V.tab_im_d + 4 * idx));
 }
-__device__ __forceinline__ float recip(float a) { return __frcp_rn(a); }
+// 1/a for the node task's division by a lane product of modulus in [1/2, 2)
+// (FP32: the hardware's approximate reciprocal, within about an ulp).
+__device__ __forceinline__ float recip(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
 __device__ __forceinline__ double recip(double a) { return __drcp_rn(a); }
 
 // Where the warp tasks read the constraint data from: global memory, or the
@@ -257,16 +263,29 @@ __device__ __forceinline__ void scatter_f(const Acc &acc, uint32_t lp, R val, in
 }
 
 // R consecutive packed literals of this lane (R a multiple of 4, 16-byte aligned).
+// (R a multiple of 4: 16-byte loads from a 16-byte aligned lane start; R = 10
+// or 14: 8-byte loads from an 8-byte aligned one.)
 template <int RL>
 __device__ __forceinline__ void load_lits(const int32_t *p, uint32_t (&lp)[RL]) {
-    const int4 *q = reinterpret_cast<const int4 *>(p);
+    if constexpr (RL % 4 == 0) {
+        const int4 *q = reinterpret_cast<const int4 *>(p);
 #pragma unroll
-    for (int k = 0; k < RL / 4; ++k) {
-        const int4 t = q[k];
-        lp[4 * k + 0] = (uint32_t)t.x;
-        lp[4 * k + 1] = (uint32_t)t.y;
-        lp[4 * k + 2] = (uint32_t)t.z;
-        lp[4 * k + 3] = (uint32_t)t.w;
+        for (int k = 0; k < RL / 4; ++k) {
+            const int4 t = q[k];
+            lp[4 * k + 0] = (uint32_t)t.x;
+            lp[4 * k + 1] = (uint32_t)t.y;
+            lp[4 * k + 2] = (uint32_t)t.z;
+            lp[4 * k + 3] = (uint32_t)t.w;
+        }
+    } else {
+        static_assert(RL % 2 == 0, "literals per lane must be even");
+        const int2 *q = reinterpret_cast<const int2 *>(p);
+#pragma unroll
+        for (int k = 0; k < RL / 2; ++k) {
+            const int2 t = q[k];
+            lp[2 * k + 0] = (uint32_t)t.x;
+            lp[2 * k + 1] = (uint32_t)t.y;
+        }
     }
 }
 
@@ -665,7 +684,8 @@ __device__ __forceinline__ void node_task_im(const DevView &V, const Src &S, int
 }
 
 // A node task of either form, nr literals per lane (task bits 16..23): a kernel
-// built for NR = 16 also runs 12 and 8, one built for NR = 8 runs 8.
+// built for NR = 16 also runs 12 and 8 (both forms) and, in FP32, 14 and 10
+// (imaginary form); one built for NR = 8 runs 8.
 template <typename R, int NR, int NI, bool SF, int XG, typename Acc>
 __device__ __forceinline__ void node_dispatch(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
                                               const Acc &acc, bool want_g, R &facc, bool want_f = true) {
@@ -673,9 +693,21 @@ __device__ __forceinline__ void node_dispatch(const DevView &V, const Src &S, in
     if (V.node_form == NODE_FORM_IMAG) {
         const bool full = ((task.x >> 8) & 0xff) == 32;
         if constexpr (NR >= 16) {
-            if (nr == 12) {
+            // 14 and 10 literals per lane: FP32 images only (the host never builds them for FP64)
+            constexpr bool kOdd = sizeof(R) == 4;
+            if (kOdd && nr == 14) {
+                if constexpr (kOdd) {
+                    if (full) node_task_im<R, 14, true, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
+                    else node_task_im<R, 14, false, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
+                }
+            } else if (nr == 12) {
                 if (full) node_task_im<R, 12, true, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
                 else node_task_im<R, 12, false, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
+            } else if (kOdd && nr == 10) {
+                if constexpr (kOdd) {
+                    if (full) node_task_im<R, 10, true, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
+                    else node_task_im<R, 10, false, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
+                }
             } else if (nr == 8) {
                 if (full) node_task_im<R, 8, true, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
                 else node_task_im<R, 8, false, XG>(V, S, task, lane, xrow, acc, want_g, facc, want_f);
