@@ -6,12 +6,14 @@
 //
 //   * every CTA holds the point's x in its shared memory and evaluates the warp
 //     tasks r, r + CL, r + 2 CL, ... (r = its rank in the cluster) into its own
-//     gradient buffer;
+//     gradient buffer, in fixed point (Fix64Acc: two native 32-bit
+//     shared-memory reductions per contribution, no compare-and-swap loops);
 //   * the cluster barrier (release / acquire) makes the CL partial gradients
 //     visible to the whole cluster;
-//   * every CTA sums the CL partials of each variable in rank order through
-//     distributed shared memory and takes the same step
-//     x <- clip(x - lr g, -1, 1) on its own copy, so the copies stay identical.
+//   * every CTA sums the CL partials of each variable through distributed
+//     shared memory and takes the same step x <- clip(x - lr g, -1, 1) on its
+//     own copy, so the copies stay identical.  Integer sums do not depend on
+//     the order of the additions: the step is bit-reproducible.
 //
 // Two gradient buffers alternate between iterations: the buffer a CTA clears
 // after the barrier of iteration k was last read by its peers before that
@@ -48,56 +50,108 @@ __device__ __forceinline__ void cluster_barrier() {
 }
 
 // Element v of the shared array `local` as held by CTA `rank` of the cluster.
-__device__ __forceinline__ double ld_peer(const double *local, int v, int rank) {
+__device__ __forceinline__ uint2 ld_peer(const uint2 *local, int v, int rank) {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(local + v);
     uint32_t ra;
-    double x;
+    uint2 x;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
-    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(x) : "r"(ra) : "memory");
+    asm volatile("ld.shared::cluster.v2.u32 {%0, %1}, [%2];" : "=r"(x.x), "=r"(x.y) : "r"(ra) : "memory");
     return x;
 }
 
-// The warp tasks t with t mod CL = rank, pulled in order from the CTA's counter;
-// gradient contributions go to G.  The counter is never reset: every warp pulls
-// until its first pull past this CTA's n_local tasks, so an iteration makes
-// exactly n_local + (warps per CTA) pulls and iteration `it` owns the pulls from
+// Clause task of the cluster step (clause3 path, see clause_task): the weight
+// is scaled by 2^S64 once, and the last multiplication of every contribution
+// is the fixed-point rounding FMA, so a contribution costs no FP64 operation
+// beyond its own product.  Negated literals flip the sign of the first factor.
+template <int CPL, bool XOR>
+__device__ __forceinline__ void clause_task_fix(const DevView &V, const Src &S, int4 task, int lane,
+                                                const double *xrow, const Fix64Acc &acc) {
+    constexpr double M = Fix64Acc::kRound;
+    const int n = V.n;
+    int4 cl[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) cl[k] = S.clauses[task.y + k * 32 + lane];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const double ws = __ldg(&V.clause_wd[task.y + k * 32 + lane]) * acc.s;
+        const uint32_t l0 = (uint32_t)cl[k].x, l1 = (uint32_t)cl[k].y, l2 = (uint32_t)cl[k].z;
+        const double y0 = gather<double, SMEM_FULL>(xrow, l0, n);
+        const double y1 = gather<double, SMEM_FULL>(xrow, l1, n);
+        const double y2 = gather<double, SMEM_FULL>(xrow, l2, n);
+        double m0, m1, m2;
+        if constexpr (XOR) {  // FE = w y0 y1 y2 (one of them the dummy)
+            const double wy2 = ws * y2;
+            m0 = fma(flip(wy2, l0), y1, M);
+            m1 = fma(flip(wy2, l1), y0, M);
+            m2 = fma(flip(ws, l2), y0 * y1, M);
+        } else {  // FE = 2 w q0 q1 q2 - w, q = (1 + y) / 2
+            const double q0 = 0.5 + 0.5 * y0;
+            const double q1 = 0.5 + 0.5 * y1;
+            const double q2 = 0.5 + 0.5 * y2;
+            const double wq0 = ws * q0;
+            m0 = fma(flip(ws, l0), q1 * q2, M);
+            m1 = fma(flip(wq0, l1), q2, M);
+            m2 = fma(flip(wq0, l2), q1, M);
+        }
+        if ((l0 & kVarMask) < (uint32_t)n) acc.put(l0 & kVarMask, m0);
+        if ((l1 & kVarMask) < (uint32_t)n) acc.put(l1 & kVarMask, m1);
+        if ((l2 & kVarMask) < (uint32_t)n) acc.put(l2 & kVarMask, m2);
+    }
+}
+
+// One warp task of the cluster step.
+template <typename R, int NR, int NI, int XG>
+__device__ __forceinline__ void cluster_task(const DevView &V, const Src &S, int4 task, int lane, const R *xrow,
+                                             const Fix64Acc &G) {
+    constexpr bool SF = false;  // FP64 node factors are recomputed in the prefix pass
+    R facc = R(0);              // the objective is not needed by a fixed-step call
+    const int kind = task.x & 0xff;
+    const bool xr = kind == TASK_XOR2;
+    if (kind == TASK_CLAUSE || xr) {
+        if (task.z == 128) {
+            if (xr) clause_task_fix<4, true>(V, S, task, lane, xrow, G);
+            else clause_task_fix<4, false>(V, S, task, lane, xrow, G);
+        } else if (task.z == 64) {
+            if (xr) clause_task_fix<2, true>(V, S, task, lane, xrow, G);
+            else clause_task_fix<2, false>(V, S, task, lane, xrow, G);
+        } else {
+            if (xr) clause_task_fix<1, true>(V, S, task, lane, xrow, G);
+            else clause_task_fix<1, false>(V, S, task, lane, xrow, G);
+        }
+    } else if (kind == TASK_PROD) {
+        prod_task<R, XG>(V, S, task, lane, xrow, G, true, facc);
+    } else {
+        node_dispatch<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
+    }
+}
+
+// The warp tasks t with t mod CL = rank into G.  At most one task per warp:
+// warp w takes local task w (no counter).  Otherwise the tasks are pulled in
+// order from the CTA's counter, which is never reset: every warp pulls until
+// its first pull past this CTA's n_local tasks, so an iteration makes exactly
+// n_local + (warps per CTA) pulls and iteration `it` owns the pulls from
 // it * (n_local + warps) on.  The caller separates iterations by barriers (the
 // cluster barrier after the evaluation, a CTA barrier after the update) and
 // zeroes the counter before the first.
-template <typename R, int NR, int NI, int XG, typename Acc>
-__device__ __forceinline__ void eval_tasks_strided(const DevView &V, const Src &S, const R *xrow, const Acc &G,
+template <typename R, int NR, int NI, int XG>
+__device__ __forceinline__ void eval_tasks_strided(const DevView &V, const Src &S, const R *xrow, const Fix64Acc &G,
                                                    int &s_ctr, int rank, int CL, int it) {
-    constexpr bool SF = false;  // FP64 node factors are recomputed in the prefix pass
     const int lane = threadIdx.x & 31;
+    const int warps = (int)(blockDim.x >> 5);
     const int n_local = (V.n_task - rank + CL - 1) / CL;
+    if (n_local <= warps) {
+        const int tl = (int)(threadIdx.x >> 5);
+        if (tl < n_local) cluster_task<R, NR, NI, XG>(V, S, S.tasks[tl * CL + rank], lane, xrow, G);
+        return;
+    }
     // unsigned: the counter and the base wrap together for any T
-    const unsigned base = (unsigned)it * (unsigned)(n_local + (int)(blockDim.x >> 5));
-    R facc = R(0);  // the objective is not needed by a fixed-step call
+    const unsigned base = (unsigned)it * (unsigned)(n_local + warps);
     for (;;) {
         unsigned t = 0;
         if (lane == 0) t = atomicAdd(reinterpret_cast<unsigned *>(&s_ctr), 1u);
         const int tl = (int)(__shfl_sync(kFull, t, 0) - base);
         if (tl >= n_local) break;
-        const int tg = tl * CL + rank;
-        const int4 task = S.tasks[tg];
-        const int kind = task.x & 0xff;
-        const bool xr = kind == TASK_XOR2;
-        if (kind == TASK_CLAUSE || xr) {
-            if (task.z == 128) {
-                if (xr) clause_task<R, XG, 4, true>(V, S, task, lane, xrow, G, true, facc);
-                else clause_task<R, XG, 4, false>(V, S, task, lane, xrow, G, true, facc);
-            } else if (task.z == 64) {
-                if (xr) clause_task<R, XG, 2, true>(V, S, task, lane, xrow, G, true, facc);
-                else clause_task<R, XG, 2, false>(V, S, task, lane, xrow, G, true, facc);
-            } else {
-                if (xr) clause_task<R, XG, 1, true>(V, S, task, lane, xrow, G, true, facc);
-                else clause_task<R, XG, 1, false>(V, S, task, lane, xrow, G, true, facc);
-            }
-        } else if (kind == TASK_PROD) {
-            prod_task<R, XG>(V, S, task, lane, xrow, G, true, facc);
-        } else {
-            node_dispatch<R, NR, NI, SF, XG>(V, S, task, lane, xrow, G, true, facc);
-        }
+        cluster_task<R, NR, NI, XG>(V, S, S.tasks[tl * CL + rank], lane, xrow, G);
     }
 }
 
@@ -116,8 +170,9 @@ __global__ void __launch_bounds__(THREADS, 1) fused_cluster_kernel(const DevView
     const int npad = (n + 2 + 3) & ~3;
     const int tid = threadIdx.x;
     R *xs = reinterpret_cast<R *>(smem_raw);
-    R *const g0 = xs + npad;
-    R *const g1 = reinterpret_cast<R *>(smem_raw + g1_off);
+    using U = uint2;
+    U *const g0 = reinterpret_cast<U *>(xs + npad);
+    U *const g1 = reinterpret_cast<U *>(smem_raw + g1_off);
     const R *x_in = static_cast<const R *>(A.x_in);
     R *x_out = static_cast<R *>(A.x_out);
     const size_t rowoff = (size_t)b * (size_t)n;
@@ -133,26 +188,37 @@ __global__ void __launch_bounds__(THREADS, 1) fused_cluster_kernel(const DevView
     }
     if (bad && rank == 0) atomicOr(V.status, STATUS_NAN);
     for (int v = tid; v < npad; v += THREADS) {
-        g0[v] = R(0);
-        g1[v] = R(0);
+        g0[v] = make_uint2(0u, 0u);
+        g1[v] = make_uint2(0u, 0u);
     }
     if (tid == 0) sh.ctr = 0;
     __syncthreads();
-    const R lr = R(A.sp.lr);
+    // x - lr g with g = (hi 2^L + lo) 2^-S64: lr 2^-S64 is exact (a power-of-two scaling)
+    const R lrs = R(A.sp.lr) * V.fix64_i;
+    const int fl = V.fix64_l;
+    Fix64Acc G;
+    G.s = V.fix64_s;
+    G.l = fl;
     for (int it = 0; it < A.sp.T; ++it) {
-        R *const gw = (it & 1) ? g1 : g0;
-        R *const gz = (it & 1) ? g0 : g1;
-        PlainAcc<R> G;
+        U *const gw = (it & 1) ? g1 : g0;
+        U *const gz = (it & 1) ? g0 : g1;
         G.g = gw;
         eval_tasks_strided<R, NR, NI, SMEM_FULL>(V, S, xs, G, sh.ctr, rank, CL, it);
         cluster_barrier();  // also ends the evaluation of this CTA's warps
         for (int v = tid; v < n; v += THREADS) {
-            R g = R(0);
-            for (int q = 0; q < CL; ++q) g += ld_peer(gw, v, q);
-            R z = xs[v] - lr * g;
-            z = z < R(-1) ? R(-1) : (z > R(1) ? R(1) : z);
-            xs[v] = z;
-            gz[v] = R(0);
+            long long hs = 0;
+            unsigned long long ls = 0;
+            for (int q = 0; q < CL; ++q) {
+                const uint2 p = ld_peer(gw, v, q);
+                ls += p.x;
+                hs += (int)p.y;
+            }
+            const long long gi = (long long)((unsigned long long)hs << fl) + (long long)ls;
+            // clip to [-1, 1] on the integer pipes: |z| > 1 becomes sign(z) 1
+            long long zb = __double_as_longlong(fma(-lrs, R(gi), xs[v]));
+            if ((zb & 0x7fffffffffffffffll) > 0x3ff0000000000000ll) zb = (zb & (long long)0x8000000000000000ull) | 0x3ff0000000000000ll;
+            xs[v] = __longlong_as_double(zb);
+            gz[v] = make_uint2(0u, 0u);
         }
         __syncthreads();  // x and the cleared buffer before the next evaluation
     }

@@ -160,6 +160,9 @@ struct ffsat_instance {
     double f_const = 0.0;        // constants of the fused kernel's f (see fill_weights)
     double f_const_plain = 0.0;  // sum of w FE over constant constraints
     float fix_s1 = 1.0f, fix_s2 = 1.0f, fix_i1 = 1.0f, fix_i12 = 1.0f;
+    double fix64_s = 1.0, fix64_i = 1.0;
+    int32_t fix64_l = 0;
+    bool fix64_ok = false;  // the cluster step's fixed point resolves 2^-44 or finer
     std::vector<int64_t> row_ptr;  // host copy of the CSR (fixed-point scales)
     std::vector<int32_t> lits_in;
     // resident images (index 0: FP32 task list, 1: FP64 task list), each with the
@@ -548,6 +551,14 @@ FusedFn launcher_for(bool f64, int nr) {
 // exactly (|c 2^S1| < 2^22) and never exceeds 2^30 in sum (Dmax = largest
 // weighted variable degree); the residual lies in [-1/2, 1/2], so with
 // S2 = min(22, 30 - ceil(log2 degmax)) the lo word is exact and bounded too.
+// The FP64 cluster step rounds each contribution to an integer V = c 2^S64
+// and adds it as two 32-bit words, lo = V mod 2^L and hi = floor(V / 2^L):
+// L = 32 - ceil(log2(degmax + 1)) keeps the lo sums below 2^32, and
+// S64 = min(30 + L - e_d, 50 - e_w) keeps the hi sums below 2^31 and |V| below
+// 2^51 (the range of the kernel's one-FMA rounding).  At unit weights that is
+// 2^-50 per contribution, near FP64's own rounding of the sums it replaces;
+// coarser than 2^-44 (very high degrees or weights) the library keeps one CTA
+// per point.
 void fixed_point_scales(ffsat_instance *I) {
     std::vector<double> D((size_t)I->n, 0.0);
     std::vector<int32_t> deg((size_t)I->n, 0);
@@ -579,6 +590,12 @@ void fixed_point_scales(ffsat_instance *I) {
     I->fix_s2 = std::ldexp(1.0f, S2);
     I->fix_i1 = std::ldexp(1.0f, -S1);
     I->fix_i12 = std::ldexp(1.0f, -(S1 + S2));
+    const int L = 32 - (int)std::ceil(std::log2((double)gmax + 1.0));
+    const int S64 = std::min(30 + L - e_d, 50 - e_w);
+    I->fix64_s = std::ldexp(1.0, S64);
+    I->fix64_i = std::ldexp(1.0, -S64);
+    I->fix64_l = L;
+    I->fix64_ok = S64 >= 44 && L >= 1;
 }
 
 void fill_weights(ffsat_instance *I) {
@@ -1411,6 +1428,9 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     V.fix_s2 = P->fix_s2;
     V.fix_i1 = P->fix_i1;
     V.fix_i12 = P->fix_i12;
+    V.fix64_s = P->fix64_s;
+    V.fix64_i = P->fix64_i;
+    V.fix64_l = P->fix64_l;
     V.row_ptr = reinterpret_cast<const int32_t *>(base + o_rp);
     V.lits = reinterpret_cast<const int32_t *>(base + o_lits);
     V.type = reinterpret_cast<const uint8_t *>(base + o_type);
@@ -1493,6 +1513,9 @@ int ffsat_set_weights(ffsat_instance *I, const double *weights) {
         W->fix_s2 = I->fix_s2;
         W->fix_i1 = I->fix_i1;
         W->fix_i12 = I->fix_i12;
+        W->fix64_s = I->fix64_s;
+        W->fix64_i = I->fix64_i;
+        W->fix64_l = I->fix64_l;
     }
     return FFSAT_OK;
 }
@@ -1521,7 +1544,7 @@ static ClusterFn cluster_launcher(int nr) {
 // dynamic shared memory and the offset of its second gradient buffer.
 static int step_cluster_size(ffsat_instance *I, int32_t B, int mode, size_t &smem, size_t &g1_off) {
     const int opt = I->opt.cluster;
-    if (opt == 1 || (mode != SMEM_FULL && mode != SMEM_RES)) return 1;
+    if (opt == 1 || (mode != SMEM_FULL && mode != SMEM_RES) || !I->fix64_ok) return 1;
     const size_t npad = ((size_t)I->n + 2 + 3) & ~size_t(3);
     g1_off = (I->smem64 + 15) & ~size_t(15);
     smem = g1_off + npad * sizeof(double);

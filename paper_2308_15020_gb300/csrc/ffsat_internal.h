@@ -104,6 +104,11 @@ struct DevView {
     // Two-word fixed-point gradient accumulator of the FP32 shared-resident mode:
     // g = hi / 2^S1 + lo / 2^(S1+S2); fix_s1 = 2^S1, fix_s2 = 2^S2 and the inverses.
     float fix_s1, fix_s2, fix_i1, fix_i12;
+    // fixed-point gradient of the FP64 cluster step, two 32-bit words per
+    // variable: g = (hi 2^L + lo) / 2^S64; fix64_s = 2^S64, fix64_i = 2^-S64,
+    // fix64_l = L
+    double fix64_s, fix64_i;
+    int32_t fix64_l, pad3;
     // start value of both fixed-point words of variable v (npad entries):
     // -(fixed-point contributions v receives per evaluation) * 0x4B400000 mod 2^32
     const int32_t *fix_bias;

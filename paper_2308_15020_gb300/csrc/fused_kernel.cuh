@@ -211,6 +211,34 @@ struct PlainAcc {
     __device__ __forceinline__ void zero(int v) const { g[v] = R(0); }
 };
 
+// Fixed point of the FP64 cluster step: each contribution c is rounded to the
+// integer V = c 2^S64, split into lo = V mod 2^L and hi = floor(V / 2^L), and
+// the two words are added with native 32-bit shared-memory reductions (a
+// 64-bit shared-memory add would be a compare-and-swap loop).  Integer sums are
+// the same in any order, so the step is bit-reproducible; the host's choice of
+// S64 and L keeps |V| below 2^51, every lo sum below 2^32 and every hi sum
+// below 2^31.  The rounding is one FMA: for |a b| < 2^51, fma(a, b, 1.5 2^52)
+// lies in [2^52, 2^53), where the spacing of doubles is 1, so it equals
+// 1.5 2^52 + round(a b) and its bit pattern minus that of 1.5 2^52 is the
+// integer.
+struct Fix64Acc {
+    static constexpr double kRound = 6755399441055744.0;  // 1.5 * 2^52
+    uint2 *g;  // {lo, hi} per variable
+    double s;
+    int l;
+    // m = fma(a, b, kRound): adds round(a b) to variable v
+    __device__ __forceinline__ void put(uint32_t v, double m) const {
+        const long long V = __double_as_longlong(m) - __double_as_longlong(kRound);
+        const unsigned lo = (unsigned)V & ((1u << l) - 1u);
+        const int hi = (int)(V >> l);
+        const unsigned a = (unsigned)__cvta_generic_to_shared(&g[v]);
+        asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(lo) : "memory");
+        asm volatile("red.shared.add.s32 [%0+4], %1;" ::"r"(a), "r"(hi) : "memory");
+    }
+    __device__ __forceinline__ void add(uint32_t v, double c) const { put(v, fma(c, s, kRound)); }
+    __device__ __forceinline__ void addf(uint32_t v, double c) const { add(v, c); }
+};
+
 // Clause and node contributions (bounded by their weight) go to the fixed-point
 // words; product contributions (XOR and long clauses, whose gradients are
 // products of many factors and can be far below the fixed-point resolution)
