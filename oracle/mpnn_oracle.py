@@ -4,7 +4,11 @@ INFRASTRUCTURE ONLY (used by tests/ to check the CUDA forward and backward).
 The architecture, features and parameter layout are the ones documented at
 ffsat_mpnn_create in include/ffsat.h; this file shares no code with the CUDA
 library.  Weights can be rounded to BF16 (round to nearest even) to mirror the
-kernels' weight precision."""
+kernels' weight precision, and the inputs of every dense product (activations
+in the forward pass, back-propagated gradients and activations in the
+backward pass) likewise, as the tensor-core dense layers take BF16 operands
+with FP32 sums; biases, bias gradients, aggregations and the output head stay
+unrounded."""
 from __future__ import annotations
 
 import numpy as np
@@ -89,19 +93,24 @@ def graph(inst):
     return S, fv, fc, deg, ln
 
 
-def forward(P, G, layers):
+def _identity(a):
+    return a
+
+
+def forward(P, G, layers, q=_identity):
+    """q rounds the inputs of each dense product (bf16, or the identity)."""
     S, fv, fc, deg, ln = G
     Sc = S / ln[:, None]                                   # mean over a constraint's literals
     Sv = (S / np.where(deg > 0, deg, 1)[None, :]).T        # mean over a variable's occurrences
     cache = {}
     relu = lambda a: np.maximum(a, 0.0)
-    hv = relu(fv @ P["Wv0"].T + P["bv0"]); hc = relu(fc @ P["Wc0"].T + P["bc0"])
+    hv = relu(q(fv) @ P["Wv0"].T + P["bv0"]); hc = relu(q(fc) @ P["Wc0"].T + P["bc0"])
     cache["hv0"], cache["hc0"] = hv, hc
     for l in range(layers):
-        mc = Sc @ (hv @ P[f"A{l}"].T)
-        hc_new = relu(np.concatenate([hc, mc], 1) @ P[f"Uc{l}"].T + P[f"buc{l}"])
-        mv = Sv @ (hc_new @ P[f"B{l}"].T)
-        hv_new = relu(np.concatenate([hv, mv], 1) @ P[f"Uv{l}"].T + P[f"buv{l}"])
+        mc = Sc @ (q(hv) @ P[f"A{l}"].T)
+        hc_new = relu(q(np.concatenate([hc, mc], 1)) @ P[f"Uc{l}"].T + P[f"buc{l}"])
+        mv = Sv @ (q(hc_new) @ P[f"B{l}"].T)
+        hv_new = relu(q(np.concatenate([hv, mv], 1)) @ P[f"Uv{l}"].T + P[f"buv{l}"])
         cache[f"mc{l}"], cache[f"mv{l}"] = mc, mv
         cache[f"hc{l + 1}"], cache[f"hv{l + 1}"] = hc_new, hv_new
         hv, hc = hv_new, hc_new
@@ -109,9 +118,12 @@ def forward(P, G, layers):
     return z, cache
 
 
-def loss_and_grad(p, inst, target, layers, bf16_weights=True):
+def loss_and_grad(p, inst, target, layers, bf16_weights=True, bf16_inputs=True):
     """Loss mean softplus(-t z) and its gradient w.r.t. the parameter vector
-    (w.r.t. the BF16-rounded weights when bf16_weights, as the kernels compute)."""
+    (w.r.t. the BF16-rounded weights when bf16_weights, and with the inputs of
+    every dense product rounded to BF16 when bf16_inputs, as the kernels
+    compute)."""
+    q = bf16 if bf16_inputs else _identity
     P = unpack(p, layers)
     if bf16_weights:
         for k in P:
@@ -121,7 +133,7 @@ def loss_and_grad(p, inst, target, layers, bf16_weights=True):
     S, fv, fc, deg, ln = G
     Sc = S / ln[:, None]
     Sv = (S / np.where(deg > 0, deg, 1)[None, :]).T
-    z, cache = forward(P, G, layers)
+    z, cache = forward(P, G, layers, q)
     t = np.asarray(target, dtype=np.float64)
     n = len(z)
     u = -t * z
@@ -138,27 +150,27 @@ def loss_and_grad(p, inst, target, layers, bf16_weights=True):
         hv_l, hc_l = cache[f"hv{l + 1}"], cache[f"hc{l + 1}"]
         mv, mc = cache[f"mv{l}"], cache[f"mc{l}"]
         d = dhv * (hv_l > 0)
-        g[f"Uv{l}"] += d.T @ np.concatenate([hv_prev, mv], 1)
+        g[f"Uv{l}"] += q(d).T @ q(np.concatenate([hv_prev, mv], 1))
         g[f"buv{l}"] += d.sum(0)
-        dcat = d @ P[f"Uv{l}"]
+        dcat = q(d) @ P[f"Uv{l}"]
         dhv_prev, dmv = dcat[:, :H], dcat[:, H:]
         dtc = Sv.T @ dmv
-        g[f"B{l}"] += dtc.T @ hc_l
-        dhc = dhc + dtc @ P[f"B{l}"]
+        g[f"B{l}"] += q(dtc).T @ q(hc_l)
+        dhc = dhc + q(dtc) @ P[f"B{l}"]
         d = dhc * (hc_l > 0)
-        g[f"Uc{l}"] += d.T @ np.concatenate([hc_prev, mc], 1)
+        g[f"Uc{l}"] += q(d).T @ q(np.concatenate([hc_prev, mc], 1))
         g[f"buc{l}"] += d.sum(0)
-        dcat = d @ P[f"Uc{l}"]
+        dcat = q(d) @ P[f"Uc{l}"]
         dhc_prev, dmc = dcat[:, :H], dcat[:, H:]
         dtv = Sc.T @ dmc
-        g[f"A{l}"] += dtv.T @ hv_prev
-        dhv = dhv_prev + dtv @ P[f"A{l}"]
+        g[f"A{l}"] += q(dtv).T @ q(hv_prev)
+        dhv = dhv_prev + q(dtv) @ P[f"A{l}"]
         dhc = dhc_prev
     d = dhv * (cache["hv0"] > 0)
-    g["Wv0"] += d.T @ fv
+    g["Wv0"] += q(d).T @ q(fv)
     g["bv0"] += d.sum(0)
     d = dhc * (cache["hc0"] > 0)
-    g["Wc0"] += d.T @ fc
+    g["Wc0"] += q(d).T @ q(fc)
     g["bc0"] += d.sum(0)
     lay, total = layout(layers)
     flat = np.zeros(total)

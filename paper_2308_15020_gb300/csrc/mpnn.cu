@@ -13,23 +13,27 @@
 // s_cv = +1 for a positive literal, -1 for a negated one.  Loss for sign targets
 // t in {-1,+1}: mean_v softplus(-t_v z_v).
 //
-// Weights are kept in FP32 (master copy, Adam state) and used by the forward and
-// backward kernels as BF16, with FP32 accumulation.  Every aggregation is a
+// Weights are kept in FP32 (master copy, Adam state) and used by the dense
+// layers as BF16; the dense layers run on the tensor cores (tcgen05) with their
+// inputs rounded to BF16 and FP32 accumulation.  Every aggregation is a
 // deterministic gather over a CSR structure (constraint -> literals, or the
 // transposed variable -> occurrences); only the weight-gradient reduction over
-// rows uses FP32 atomics.
+// row tiles uses FP32 atomics.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
 #include <vector>
 
 #include "ffsat.h"
 #include "ffsat_internal.h"
 #include "fused_kernel.cuh"
+#include "mpnn_tc.cuh"
 
 namespace ffsat {
 namespace mp {
@@ -42,183 +46,271 @@ constexpr uint32_t kSign = 0x80000000u;
 constexpr uint32_t kIdx = 0x7fffffffu;
 
 // ---------------------------------------------------------------------------
-// dense layer: Y[r, :] = act(W [X1[r, :]; X2[r, :]] + b), W is N x (K1 + K2), N = H.
-// Register-tiled FP32 SIMT GEMMs: a CTA owns TR rows, each thread a 4 x 4 block of
-// the output; operands are staged in shared memory in 64-column chunks of the
-// concatenated input, W transposed to [k][o] so that lanes read consecutive
-// banks.  K1 and K2 are multiples of 4, K1 + K2 <= 2H.  Every output element
-// sums its terms in the order bias, k = 0 .. K-1 (fwd) and o = 0 .. H-1 (dX).
+// Dense layers on the tensor cores (mpnn_tc.cuh): one CTA of four warps per
+// 128-row tile, BF16 operands (inputs rounded to nearest even, weights stored in
+// BF16), FP32 accumulation in TMEM.  Input widths K1 + K2 are multiples of 8
+// (8, 64 or 128) and padded with zeros to a multiple of 16 (the K of one MMA).
+//   forward:  Y = act([X1, X2] W^T + b)        A = [X1, X2] rows, B = W (H x K)
+//   dX:       [dX1, dX2] = dY W                A = dY rows, B = W^T (K x H)
+//   dW:       dW += dY^T [X1, X2], db += sum dY   A = [X1, X2]^T (K x rows), B = dY^T
+// Each output element is one FP32 tensor-core sum over its K terms (the bias is
+// added after it); dW and db add each CTA's sum with one FP32 atomic.
 // ---------------------------------------------------------------------------
-constexpr int TR = 32;       // rows per CTA tile
-constexpr int KC = 64;       // input columns per shared-memory chunk
-constexpr int XP = KC + 4;   // padded row pitch of the staged inputs (keeps float4 alignment)
-constexpr int FWD_THREADS = (TR / 4) * (H / 4);  // 128
+constexpr int TCR = tc::kRows;
+constexpr int TCT = tc::kThreads;
+// dynamic shared memory of every dense launch: at most four CTAs per SM, so
+// that four TMEM allocations of at most 128 columns never exceed the SM's 512
+constexpr size_t kDenseSmem = 56 * 1024;
 
-__device__ __forceinline__ float concat_at(const float *__restrict__ X1, int K1, const float *__restrict__ X2, int K2,
-                                           int r, int k) {
-    return k < K1 ? X1[(size_t)r * K1 + k] : X2[(size_t)r * K2 + (k - K1)];
+__device__ __forceinline__ const float *concat_row(const float *__restrict__ X1, int K1, const float *__restrict__ X2,
+                                                   int K2, int r, int k) {
+    return k < K1 ? X1 + (size_t)r * K1 + k : X2 + (size_t)r * K2 + (k - K1);
+}
+
+__device__ __forceinline__ void load8(const float *p, float *v) {
+    const float4 a = __ldg(reinterpret_cast<const float4 *>(p));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(p + 4));
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+}
+
+// TMEM allocation and mbarrier set-up at the start of a dense kernel; the
+// caller's barrier (with the tcgen05 fences) publishes both.
+__device__ __forceinline__ void tc_setup(uint32_t *holder, uint64_t *bar, uint32_t ncols) {
+    if ((threadIdx.x >> 5) == 0) tc::tmem_alloc(holder, ncols);
+    if (threadIdx.x == 0) tc::mbar_init(bar, 1);
+}
+
+// Operands staged: publish them to the tensor core and the TMEM address to all threads.
+__device__ __forceinline__ uint32_t tc_publish(const uint32_t *holder) {
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    return *holder;
+}
+
+// End of a dense kernel: every TMEM read done, warp 0 frees the columns.
+__device__ __forceinline__ void tc_teardown(uint32_t tmem, uint32_t ncols) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if ((threadIdx.x >> 5) == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, ncols);
+    }
+}
+
+// One thread issues the Kp / 16 MMAs of a tile (A and B K-major, kc8 = Kp / 8
+// column groups each) and commits them to bar.
+__device__ __forceinline__ void tc_issue(uint32_t tmem, const unsigned char *As, const unsigned char *Bs, int kc8,
+                                         int ksteps, uint32_t idesc, bool acc_first, uint64_t *bar) {
+    const uint32_t a0 = tc::smem_u32(As), b0 = tc::smem_u32(Bs), sbo = (uint32_t)kc8 * 128u;
+    for (int j = 0; j < ksteps; ++j)
+        tc::mma_bf16(tmem, tc::smem_desc(a0 + 256u * j, 128u, sbo), tc::smem_desc(b0 + 256u * j, 128u, sbo), idesc,
+                     acc_first || j > 0);
+    tc::mma_commit(bar);
 }
 
 template <bool RELU>
-__global__ void __launch_bounds__(FWD_THREADS) dense_fwd(const float *__restrict__ X1, int K1,
-                                                         const float *__restrict__ X2, int K2,
-                                                         const __nv_bfloat16 *__restrict__ W,
-                                                         const float *__restrict__ b, float *__restrict__ Y, int R) {
-    __shared__ __align__(16) float wt[KC][H];  // wt[k][o] = W[o][c0 + k]
-    __shared__ __align__(16) float xs[TR][XP];
+__global__ void __launch_bounds__(TCT) tc_dense_fwd(const float *__restrict__ X1, int K1,
+                                                    const float *__restrict__ X2, int K2,
+                                                    const __nv_bfloat16 *__restrict__ W,
+                                                    const float *__restrict__ b, float *__restrict__ Y, int R,
+                                                    int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t holder;
+    const int K = K1 + K2, Kp = (K + 15) & ~15, kc8 = Kp / 8;
+    unsigned char *As = smem, *Bs = smem + (size_t)TCR * Kp * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.x * TCR;
+    tc_setup(&holder, &bar, H);
+    for (int i = tid; i < TCR * kc8; i += TCT) {  // A: 128 rows of [X1, X2]
+        const int r8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
+        const int r = r0 + g * 8 + r8, k = c * 8;
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (r < R && k < K) load8(concat_row(X1, K1, X2, K2, r, k), v);
+        tc::st_chunk(As, g, c, kc8, r8, tc::pack8(v));
+    }
+    for (int i = tid; i < H * kc8; i += TCT) {  // B: W, H rows of K
+        const int n8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
+        const int n = g * 8 + n8, k = c * 8;
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (k < K) w = __ldg(reinterpret_cast<const uint4 *>(W + (size_t)n * K + k));
+        tc::st_chunk(Bs, g, c, kc8, n8, w);
+    }
+    const uint32_t tmem = tc_publish(&holder);
+    if (tid == 0) tc_issue(tmem, As, Bs, kc8, Kp / 16, tc::idesc_bf16(TCR, H), false, &bar);
+    const bool ok = tc::mbar_wait(&bar, 0);
+    tc::fence_after_sync();
+    const int r = r0 + warp * 32 + lane;
+#pragma unroll
+    for (int h = 0; h < H / 32; ++h) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * 32), v);
+        if (r < R) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                float4 o;
+                o.x = v[j] + (b ? __ldg(b + h * 32 + j) : 0.f);
+                o.y = v[j + 1] + (b ? __ldg(b + h * 32 + j + 1) : 0.f);
+                o.z = v[j + 2] + (b ? __ldg(b + h * 32 + j + 2) : 0.f);
+                o.w = v[j + 3] + (b ? __ldg(b + h * 32 + j + 3) : 0.f);
+                if (RELU) o = make_float4(fmaxf(o.x, 0.f), fmaxf(o.y, 0.f), fmaxf(o.z, 0.f), fmaxf(o.w, 0.f));
+                if (!ok) o = make_float4(__int_as_float(0x7fc00000), o.y, o.z, o.w);
+                *reinterpret_cast<float4 *>(Y + (size_t)r * H + h * 32 + j) = o;
+            }
+        }
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(err, 1);
+        (void)tc::mbar_wait(&bar, 0);
+    }
+    tc_teardown(tmem, H);
+}
+
+// [dX1, dX2] = dY W for one 128-row tile: N = K1 + K2 (64 or 128) TMEM columns.
+__global__ void __launch_bounds__(TCT) tc_dense_bwd_x(const float *__restrict__ dY,
+                                                      const __nv_bfloat16 *__restrict__ W, int K1, int K2,
+                                                      float *__restrict__ dX1, float *__restrict__ dX2, int R,
+                                                      int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t holder;
+    constexpr int kc8 = H / 8;
+    const int N = K1 + K2;
+    unsigned char *As = smem, *Bs = smem + (size_t)TCR * H * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r0 = blockIdx.x * TCR;
+    tc_setup(&holder, &bar, (uint32_t)N);
+    for (int i = tid; i < TCR * kc8; i += TCT) {  // A: 128 rows of dY
+        const int r8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
+        const int r = r0 + g * 8 + r8;
+        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (r < R) load8(dY + (size_t)r * H + c * 8, v);
+        tc::st_chunk(As, g, c, kc8, r8, tc::pack8(v));
+    }
+    for (int i = tid; i < N * kc8; i += TCT) {  // B: W^T, N rows of H (a column of W each)
+        const int n8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
+        const int j = g * 8 + n8;
+        uint4 w;
+        uint16_t *e = reinterpret_cast<uint16_t *>(&w);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) e[t] = __ldg(reinterpret_cast<const unsigned short *>(W) + (size_t)(c * 8 + t) * N + j);
+        tc::st_chunk(Bs, g, c, kc8, n8, w);
+    }
+    const uint32_t tmem = tc_publish(&holder);
+    if (tid == 0) tc_issue(tmem, As, Bs, kc8, H / 16, tc::idesc_bf16(TCR, N), false, &bar);
+    const bool ok = tc::mbar_wait(&bar, 0);
+    tc::fence_after_sync();
+    const int r = r0 + warp * 32 + lane;
+    for (int h = 0; h < N / 32; ++h) {
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * 32), v);
+        const int j0 = h * 32;
+        float *dst = j0 < K1 ? dX1 : dX2;
+        if (r < R && dst) {
+            const int pitch = j0 < K1 ? K1 : K2, jj = j0 < K1 ? j0 : j0 - K1;
+#pragma unroll
+            for (int j = 0; j < 32; j += 4) {
+                float4 o = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                if (!ok) o.x = __int_as_float(0x7fc00000);
+                *reinterpret_cast<float4 *>(dst + (size_t)r * pitch + jj + j) = o;
+            }
+        }
+    }
+    if (!ok) {
+        if (lane == 0) atomicOr(err, 1);
+        (void)tc::mbar_wait(&bar, 0);
+    }
+    tc_teardown(tmem, (uint32_t)N);
+}
+
+// dW += dY^T [X1, X2] (dW is H x K, K = K1 + K2 <= 128) and db += sum_r dY: the
+// CTA walks the 128-row tiles blockIdx.x, blockIdx.x + gridDim.x, ..., adding
+// D[k][o] = sum_r X[r][k] dY[r][o] (M = 128 >= K rows of the transposed input,
+// N = H) in TMEM over its tiles, then adds D and its column sums of dY to dW
+// and db with FP32 atomics.  Rows past K of A stay zero.
+__global__ void __launch_bounds__(TCT) tc_dense_bwd_w(const float *__restrict__ dY, const float *__restrict__ X1,
+                                                      int K1, const float *__restrict__ X2, int K2,
+                                                      float *__restrict__ dW, float *__restrict__ db, int R,
+                                                      int *__restrict__ err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t holder;
+    constexpr int kc8 = TCR / 8;  // the K of these MMAs is the tile's 128 rows
     const int K = K1 + K2;
-    const int t = threadIdx.x, tx = t % (H / 4), ty = t / (H / 4);
-    const int r0 = blockIdx.x * TR;
-    float acc[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float bj = b ? b[tx * 4 + j] : 0.f;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc[i][j] = bj;
+    unsigned char *As = smem, *Bs = smem + (size_t)TCR * TCR * 2;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    tc_setup(&holder, &bar, H);
+    // the zero rows k >= K of A, written once
+    for (int i = tid; i < TCR * kc8; i += TCT) {
+        const int k = (i >> 3) / kc8 * 8 + (i & 7);
+        if (k >= K) tc::st_chunk(As, (i >> 3) / kc8, (i >> 3) % kc8, kc8, i & 7, make_uint4(0u, 0u, 0u, 0u));
     }
-    for (int c0 = 0; c0 < K; c0 += KC) {
-        const int kc = min(KC, K - c0);  // a multiple of 4
-        __syncthreads();
-        for (int i = t; i < H * kc; i += FWD_THREADS) {
-            const int o = i % H, k = i / H;
-            wt[k][o] = __bfloat162float(W[(size_t)o * K + c0 + k]);
-        }
-        for (int i = t; i < TR * kc; i += FWD_THREADS) {
-            const int rr = i / kc, k = i % kc, r = r0 + rr;
-            xs[rr][k] = r < R ? concat_at(X1, K1, X2, K2, r, c0 + k) : 0.f;
-        }
-        __syncthreads();
-        for (int k = 0; k < kc; k += 4) {
-            float4 xv[4];
+    // thread t stages B chunks (o = 8 q + (t & 7), rows 8 (t >> 3) .. + 7) for q = 0 .. 7
+    float bsum[H / 8];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) xv[i] = *reinterpret_cast<const float4 *>(&xs[ty * 4 + i][k]);
+    for (int q = 0; q < H / 8; ++q) bsum[q] = 0.f;
+    const int tiles = (R + TCR - 1) / TCR;
+    uint32_t tmem = 0;
+    bool ok = true;
+    int done = 0;
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++done) {
+        const int r0 = tile * TCR;
+        if (done > 0) ok &= tc::mbar_wait(&bar, (uint32_t)(done - 1) & 1u);  // the MMAs have read the buffers
+        for (int i = tid; i < K * kc8; i += TCT) {  // A[k][r] = X[r][k]
+            const int k8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
+            const int k = g * 8 + k8;
+            float v[8];
 #pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const float4 wv = *reinterpret_cast<const float4 *>(&wt[k + kk][tx * 4]);
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float xi = kk == 0 ? xv[i].x : kk == 1 ? xv[i].y : kk == 2 ? xv[i].z : xv[i].w;
-                    acc[i][0] = fmaf(wv.x, xi, acc[i][0]);
-                    acc[i][1] = fmaf(wv.y, xi, acc[i][1]);
-                    acc[i][2] = fmaf(wv.z, xi, acc[i][2]);
-                    acc[i][3] = fmaf(wv.w, xi, acc[i][3]);
-                }
+            for (int t = 0; t < 8; ++t) {
+                const int r = r0 + c * 8 + t;
+                v[t] = r < R ? __ldg(concat_row(X1, K1, X2, K2, r, k)) : 0.f;
             }
+            tc::st_chunk(As, g, c, kc8, k8, tc::pack8(v));
         }
-    }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = r0 + ty * 4 + i;
-        if (r >= R) break;
-        float4 v = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-        if (RELU) v = make_float4(fmaxf(v.x, 0.f), fmaxf(v.y, 0.f), fmaxf(v.z, 0.f), fmaxf(v.w, 0.f));
-        *reinterpret_cast<float4 *>(Y + (size_t)r * H + tx * 4) = v;
-    }
-}
-
-// dX = dY W, split into the two input blocks; dY already includes the activation
-// mask.  K = K1 + K2 in {4, 8, .., 2H}; the CTA has (K / 4) * (TR / 4) threads.
-__global__ void __launch_bounds__(2 * H / 4 * (TR / 4)) dense_bwd_x(const float *__restrict__ dY,
-                                                                   const __nv_bfloat16 *__restrict__ W, int K1, int K2,
-                                                                   float *__restrict__ dX1, float *__restrict__ dX2,
-                                                                   int R) {
-    __shared__ __align__(16) float ws[H][2 * H];  // ws[o][k] = W[o][k]
-    __shared__ __align__(16) float ds[TR][H + 4];
-    const int K = K1 + K2, K4 = K / 4, nt = K4 * (TR / 4);
-    const int t = threadIdx.x, tx = t % K4, ty = t / K4;
-    const int r0 = blockIdx.x * TR;
-    for (int i = t; i < H * K; i += nt) ws[i / K][i % K] = __bfloat162float(W[i]);
-    for (int i = t; i < TR * H; i += nt) {
-        const int rr = i / H, o = i % H, r = r0 + rr;
-        ds[rr][o] = r < R ? dY[(size_t)r * H + o] : 0.f;
-    }
-    __syncthreads();
-    float acc[4][4] = {};
-    for (int o = 0; o < H; o += 4) {
-        float4 dv[4];
+        for (int q = 0; q < H / 8; ++q) {  // B[o][r] = dY[r][o]
+            const int o8 = tid & 7, c = tid >> 3, o = q * 8 + o8;
+            float v[8];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) dv[i] = *reinterpret_cast<const float4 *>(&ds[ty * 4 + i][o]);
-#pragma unroll
-        for (int oo = 0; oo < 4; ++oo) {
-            const float4 wv = *reinterpret_cast<const float4 *>(&ws[o + oo][tx * 4]);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float di = oo == 0 ? dv[i].x : oo == 1 ? dv[i].y : oo == 2 ? dv[i].z : dv[i].w;
-                acc[i][0] = fmaf(di, wv.x, acc[i][0]);
-                acc[i][1] = fmaf(di, wv.y, acc[i][1]);
-                acc[i][2] = fmaf(di, wv.z, acc[i][2]);
-                acc[i][3] = fmaf(di, wv.w, acc[i][3]);
+            for (int t = 0; t < 8; ++t) {
+                const int r = r0 + c * 8 + t;
+                v[t] = r < R ? __ldg(dY + (size_t)r * H + o) : 0.f;
+                bsum[q] += v[t];
             }
+            tc::st_chunk(Bs, q, c, kc8, o8, tc::pack8(v));
+        }
+        const uint32_t t_addr = tc_publish(&holder);
+        tmem = t_addr;
+        if (tid == 0) tc_issue(tmem, As, Bs, kc8, TCR / 16, tc::idesc_bf16(TCR, H), done > 0, &bar);
+    }
+    if (done > 0) ok &= tc::mbar_wait(&bar, (uint32_t)(done - 1) & 1u);
+    else tmem = tc_publish(&holder);
+    tc::fence_after_sync();
+    const int k = warp * 32 + lane;
+    if (done > 0) {
+#pragma unroll
+        for (int h = 0; h < H / 32; ++h) {
+            float v[32];
+            tc::tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(h * 32), v);
+            if (k < K)
+#pragma unroll
+                for (int j = 0; j < 32; ++j) atomicAdd(dW + (size_t)(h * 32 + j) * K + k, ok ? v[j] : __int_as_float(0x7fc00000));
         }
     }
-    const int k = tx * 4;
-    float *dst = k < K1 ? dX1 : dX2;
-    if (!dst) return;
-    const int pitch = k < K1 ? K1 : K2, kk = k < K1 ? k : k - K1;
+    if (db) {
+        // lanes with equal (lane & 7) hold the same o: fold the warp's four, then one atomic per o
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int r = r0 + ty * 4 + i;
-        if (r >= R) break;
-        *reinterpret_cast<float4 *>(dst + (size_t)r * pitch + kk) = make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]);
-    }
-}
-
-// dW += dY^T [X1, X2], db += sum_r dY.  A grid of at most a few CTAs per SM walks
-// the TR-row tiles; each thread keeps the 4 x 4 blocks (o, k) it owns in registers
-// across tiles and adds them to dW with one FP32 atomic per element at the end.
-constexpr int BW_THREADS = 256;
-template <int NB>  // 4 x 4 blocks per thread: 16 * K / 4 <= NB * BW_THREADS
-__global__ void __launch_bounds__(BW_THREADS) dense_bwd_w(const float *__restrict__ dY, const float *__restrict__ X1,
-                                                          int K1, const float *__restrict__ X2, int K2,
-                                                          float *__restrict__ dW, float *__restrict__ db, int R) {
-    __shared__ __align__(16) float ds[TR][H];
-    __shared__ __align__(16) float xs[TR][2 * H];
-    const int K = K1 + K2, K4 = K / 4, nblk = (H / 4) * K4;
-    const int t = threadIdx.x;
-    float acc[NB][4][4] = {};
-    float bacc = 0.f;
-    const int tiles = (R + TR - 1) / TR;
-    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int r0 = tile * TR;
-        __syncthreads();
-        for (int i = t; i < TR * H; i += BW_THREADS) {
-            const int rr = i / H, o = i % H, r = r0 + rr;
-            ds[rr][o] = r < R ? dY[(size_t)r * H + o] : 0.f;
+        for (int q = 0; q < H / 8; ++q) {
+            float s = bsum[q];
+            s += __shfl_xor_sync(0xffffffffu, s, 8);
+            s += __shfl_xor_sync(0xffffffffu, s, 16);
+            if (lane < 8) atomicAdd(db + q * 8 + lane, s);
         }
-        for (int i = t; i < TR * K; i += BW_THREADS) {
-            const int rr = i / K, k = i % K, r = r0 + rr;
-            xs[rr][k] = r < R ? concat_at(X1, K1, X2, K2, r, k) : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < NB; ++q) {
-            const int blk = t + q * BW_THREADS;
-            if (blk >= nblk) break;
-            const int o = (blk / K4) * 4, k = (blk % K4) * 4;
-            for (int rr = 0; rr < TR; ++rr) {
-                const float4 dv = *reinterpret_cast<const float4 *>(&ds[rr][o]);
-                const float4 xv = *reinterpret_cast<const float4 *>(&xs[rr][k]);
-                const float d[4] = {dv.x, dv.y, dv.z, dv.w}, x[4] = {xv.x, xv.y, xv.z, xv.w};
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c) acc[q][a][c] = fmaf(d[a], x[c], acc[q][a][c]);
-            }
-        }
-        if (db && t < H)
-            for (int rr = 0; rr < TR; ++rr) bacc += ds[rr][t];
     }
-#pragma unroll
-    for (int q = 0; q < NB; ++q) {
-        const int blk = t + q * BW_THREADS;
-        if (blk >= nblk) break;
-        const int o = (blk / K4) * 4, k = (blk % K4) * 4;
-#pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) atomicAdd(&dW[(size_t)(o + a) * K + k + c], acc[q][a][c]);
-    }
-    if (db && t < H) atomicAdd(&db[t], bacc);
+    if (!ok && lane == 0) atomicOr(err, 1);
+    tc_teardown(tmem, H);
 }
 
 // out[r, :] = (norm ? 1/cnt_r : 1) * sum_{e in row r} sign_e * scale[src_e] * src[src_e, :]
@@ -353,6 +445,7 @@ struct ffsat_mpnn {
     float *dHv = nullptr, *dHv2 = nullptr, *dHvx = nullptr, *dMv = nullptr, *dT1 = nullptr;
     float *dHc = nullptr, *dHc2 = nullptr, *dHcx = nullptr, *dMc = nullptr, *dT2 = nullptr;
     float *dz = nullptr, *x0 = nullptr;
+    int *d_err = nullptr;  // set by a dense kernel whose tensor-core wait gave up
     std::vector<void *> allocs;
 };
 
@@ -414,13 +507,28 @@ int ensure_capacity(ffsat_mpnn *M, size_t n, size_t m) {
 
 inline unsigned blocks_for(size_t threads, unsigned per) { return (unsigned)((threads + per - 1) / per); }
 
+// Raise the dynamic shared-memory limit of the dense kernels once per device.
+void dense_smem_limits() {
+    static std::mutex mu;
+    static std::set<int> done;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!done.insert(dev).second) return;
+    cudaFuncSetAttribute(tc_dense_fwd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmem);
+    cudaFuncSetAttribute(tc_dense_fwd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmem);
+    cudaFuncSetAttribute(tc_dense_bwd_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmem);
+    cudaFuncSetAttribute(tc_dense_bwd_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDenseSmem);
+}
+
 void dense(cudaStream_t s, bool relu, const float *X1, int K1, const float *X2, int K2, const __nv_bfloat16 *W,
-           const float *b, float *Y, int R) {
+           const float *b, float *Y, int R, int *err) {
     if (R <= 0) return;
+    dense_smem_limits();
     if (relu)
-        dense_fwd<true><<<blocks_for(R, TR), FWD_THREADS, 0, s>>>(X1, K1, X2, K2, W, b, Y, R);
+        tc_dense_fwd<true><<<blocks_for(R, TCR), TCT, kDenseSmem, s>>>(X1, K1, X2, K2, W, b, Y, R, err);
     else
-        dense_fwd<false><<<blocks_for(R, TR), FWD_THREADS, 0, s>>>(X1, K1, X2, K2, W, b, Y, R);
+        tc_dense_fwd<false><<<blocks_for(R, TCR), TCT, kDenseSmem, s>>>(X1, K1, X2, K2, W, b, Y, R, err);
 }
 
 void gather(cudaStream_t s, const float *src, const int32_t *ptr, const uint32_t *idx, const float *scale, int R,
@@ -439,19 +547,21 @@ int sm_count() {
     return count;
 }
 
+// Weight gradient: at most half the SMs' worth of CTAs, each summing its row
+// tiles in TMEM, so that the FP32 atomics into dW stay few.
 void dW(cudaStream_t s, const float *dY, const float *X1, int K1, const float *X2, int K2, float *gW, float *gb,
-        int R) {
+        int R, int *err) {
     if (R <= 0) return;
-    const unsigned grid = std::min<unsigned>(blocks_for(R, TR), (unsigned)sm_count());
-    if (4 * (K1 + K2) <= BW_THREADS)
-        dense_bwd_w<1><<<grid, BW_THREADS, 0, s>>>(dY, X1, K1, X2, K2, gW, gb, R);
-    else
-        dense_bwd_w<2><<<grid, BW_THREADS, 0, s>>>(dY, X1, K1, X2, K2, gW, gb, R);
+    dense_smem_limits();
+    const unsigned grid = std::min<unsigned>(blocks_for(R, TCR), (unsigned)std::max(1, sm_count() / 2));
+    tc_dense_bwd_w<<<grid, TCT, kDenseSmem, s>>>(dY, X1, K1, X2, K2, gW, gb, R, err);
 }
 
-void dX(cudaStream_t s, const float *dY, const __nv_bfloat16 *W, int K1, int K2, float *dX1, float *dX2, int R) {
+void dX(cudaStream_t s, const float *dY, const __nv_bfloat16 *W, int K1, int K2, float *dX1, float *dX2, int R,
+        int *err) {
     if (R <= 0) return;
-    dense_bwd_x<<<blocks_for(R, TR), (K1 + K2) / 4 * (TR / 4), 0, s>>>(dY, W, K1, K2, dX1, dX2, R);
+    dense_smem_limits();
+    tc_dense_bwd_x<<<blocks_for(R, TCR), TCT, kDenseSmem, s>>>(dY, W, K1, K2, dX1, dX2, R, err);
 }
 
 void mask(cudaStream_t s, float *d, const float *y, size_t count) {
@@ -466,15 +576,15 @@ int run(ffsat_mpnn *M, const GraphView &G, const float *target, float *loss, flo
     if (rc) return rc;
     const __nv_bfloat16 *P = M->pb;
     // forward
-    dense(s, true, G.fv, FV, nullptr, 0, P + M->o_wv0, M->p + M->o_bv0, M->Hv[0], n);
-    dense(s, true, G.fc, FC, nullptr, 0, P + M->o_wc0, M->p + M->o_bc0, M->Hc[0], m);
+    dense(s, true, G.fv, FV, nullptr, 0, P + M->o_wv0, M->p + M->o_bv0, M->Hv[0], n, M->d_err);
+    dense(s, true, G.fc, FC, nullptr, 0, P + M->o_wc0, M->p + M->o_bc0, M->Hc[0], m, M->d_err);
     for (int l = 1; l <= L; ++l) {
-        dense(s, false, M->Hv[l - 1], H, nullptr, 0, P + M->o_A[l - 1], nullptr, M->T1, n);
+        dense(s, false, M->Hv[l - 1], H, nullptr, 0, P + M->o_A[l - 1], nullptr, M->T1, n, M->d_err);
         gather(s, M->T1, G.row_ptr, G.lits, nullptr, m, true, M->Mc[l]);
-        dense(s, true, M->Hc[l - 1], H, M->Mc[l], H, P + M->o_Uc[l - 1], M->p + M->o_buc[l - 1], M->Hc[l], m);
-        dense(s, false, M->Hc[l], H, nullptr, 0, P + M->o_B[l - 1], nullptr, M->T2, m);
+        dense(s, true, M->Hc[l - 1], H, M->Mc[l], H, P + M->o_Uc[l - 1], M->p + M->o_buc[l - 1], M->Hc[l], m, M->d_err);
+        dense(s, false, M->Hc[l], H, nullptr, 0, P + M->o_B[l - 1], nullptr, M->T2, m, M->d_err);
         gather(s, M->T2, G.var_ptr, G.var_occ, nullptr, n, true, M->Mv[l]);
-        dense(s, true, M->Hv[l - 1], H, M->Mv[l], H, P + M->o_Uv[l - 1], M->p + M->o_buv[l - 1], M->Hv[l], n);
+        dense(s, true, M->Hv[l - 1], H, M->Mv[l], H, P + M->o_Uv[l - 1], M->p + M->o_buv[l - 1], M->Hv[l], n, M->d_err);
     }
     float *x0 = x0_out ? x0_out : M->x0;
     if (target) MP_TRY(cudaMemsetAsync(loss, 0, sizeof(float), s));
@@ -491,33 +601,33 @@ int run(ffsat_mpnn *M, const GraphView &G, const float *target, float *loss, flo
     for (int l = L; l >= 1; --l) {
         // h_v^l = relu(Uv [h_v^{l-1}; m_v] + buv)
         mask(s, dHv, M->Hv[l], (size_t)n * H);
-        dW(s, dHv, M->Hv[l - 1], H, M->Mv[l], H, M->g + M->o_Uv[l - 1], M->g + M->o_buv[l - 1], n);
-        dX(s, dHv, P + M->o_Uv[l - 1], H, H, dHv2, M->dMv, n);
+        dW(s, dHv, M->Hv[l - 1], H, M->Mv[l], H, M->g + M->o_Uv[l - 1], M->g + M->o_buv[l - 1], n, M->d_err);
+        dX(s, dHv, P + M->o_Uv[l - 1], H, H, dHv2, M->dMv, n, M->d_err);
         // m_v = (1/deg v) sum s t_c  ->  dt_c = sum_{v in c} s dm_v / deg v
         gather(s, M->dMv, G.row_ptr, G.lits, G.inv_deg, m, false, M->dT2);
         // t_c = B h_c^l
-        dW(s, M->dT2, M->Hc[l], H, nullptr, 0, M->g + M->o_B[l - 1], nullptr, m);
-        dX(s, M->dT2, P + M->o_B[l - 1], H, 0, M->dHcx, nullptr, m);
+        dW(s, M->dT2, M->Hc[l], H, nullptr, 0, M->g + M->o_B[l - 1], nullptr, m, M->d_err);
+        dX(s, M->dT2, P + M->o_B[l - 1], H, 0, M->dHcx, nullptr, m, M->d_err);
         add_inplace<<<std::min<unsigned>(blocks_for((size_t)m * H, 256), 4096), 256, 0, s>>>(dHc, M->dHcx,
                                                                                            (size_t)m * H);
         // h_c^l = relu(Uc [h_c^{l-1}; m_c] + buc)
         mask(s, dHc, M->Hc[l], (size_t)m * H);
-        dW(s, dHc, M->Hc[l - 1], H, M->Mc[l], H, M->g + M->o_Uc[l - 1], M->g + M->o_buc[l - 1], m);
-        dX(s, dHc, P + M->o_Uc[l - 1], H, H, dHc2, M->dMc, m);
+        dW(s, dHc, M->Hc[l - 1], H, M->Mc[l], H, M->g + M->o_Uc[l - 1], M->g + M->o_buc[l - 1], m, M->d_err);
+        dX(s, dHc, P + M->o_Uc[l - 1], H, H, dHc2, M->dMc, m, M->d_err);
         // m_c = (1/|c|) sum s t_v  ->  dt_v = sum_{c ni v} s dm_c / |c|
         gather(s, M->dMc, G.var_ptr, G.var_occ, G.inv_len, n, false, M->dT1);
         // t_v = A h_v^{l-1}
-        dW(s, M->dT1, M->Hv[l - 1], H, nullptr, 0, M->g + M->o_A[l - 1], nullptr, n);
-        dX(s, M->dT1, P + M->o_A[l - 1], H, 0, M->dHvx, nullptr, n);
+        dW(s, M->dT1, M->Hv[l - 1], H, nullptr, 0, M->g + M->o_A[l - 1], nullptr, n, M->d_err);
+        dX(s, M->dT1, P + M->o_A[l - 1], H, 0, M->dHvx, nullptr, n, M->d_err);
         add_inplace<<<std::min<unsigned>(blocks_for((size_t)n * H, 256), 4096), 256, 0, s>>>(dHv2, M->dHvx,
                                                                                            (size_t)n * H);
         std::swap(dHv, dHv2);
         std::swap(dHc, dHc2);
     }
     mask(s, dHv, M->Hv[0], (size_t)n * H);
-    dW(s, dHv, G.fv, FV, nullptr, 0, M->g + M->o_wv0, M->g + M->o_bv0, n);
+    dW(s, dHv, G.fv, FV, nullptr, 0, M->g + M->o_wv0, M->g + M->o_bv0, n, M->d_err);
     mask(s, dHc, M->Hc[0], (size_t)m * H);
-    dW(s, dHc, G.fc, FC, nullptr, 0, M->g + M->o_wc0, M->g + M->o_bc0, m);
+    dW(s, dHc, G.fc, FC, nullptr, 0, M->g + M->o_wc0, M->g + M->o_bc0, m, M->d_err);
     MP_TRY(cudaGetLastError());
     return FFSAT_OK;
 }
@@ -552,6 +662,14 @@ int ffsat_mpnn_create(int32_t layers, uint64_t seed, ffsat_mpnn **out) {
     M->o_wo = take(H);
     M->o_bo = take(1);
     M->n_params = off;
+    // the dense kernels read weight rows as 16-byte groups of eight BF16 values
+    bool aligned = M->o_wv0 % 8 == 0 && M->o_wc0 % 8 == 0;
+    for (int l = 0; l < layers; ++l)
+        aligned = aligned && M->o_A[l] % 8 == 0 && M->o_Uc[l] % 8 == 0 && M->o_B[l] % 8 == 0 && M->o_Uv[l] % 8 == 0;
+    if (!aligned) {
+        delete M;
+        return set_error(FFSAT_ERR_ARG, "internal: weight offsets not 16-byte aligned");
+    }
     // Glorot-uniform weights from splitmix64, zero biases
     std::vector<float> hp(off, 0.f);
     uint64_t st = seed;
@@ -577,6 +695,8 @@ int ffsat_mpnn_create(int32_t layers, uint64_t seed, ffsat_mpnn **out) {
     if (e == cudaSuccess) e = cudaMalloc(&M->m1, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&M->m2, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc(&M->pb, off * sizeof(__nv_bfloat16));
+    if (e == cudaSuccess) e = cudaMalloc(&M->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(M->d_err, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(M->p, hp.data(), off * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(M->m1, 0, off * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(M->m2, 0, off * sizeof(float));
@@ -691,6 +811,7 @@ void ffsat_mpnn_free(ffsat_mpnn *M) {
     if (M->m1) cudaFree(M->m1);
     if (M->m2) cudaFree(M->m2);
     if (M->pb) cudaFree(M->pb);
+    if (M->d_err) cudaFree(M->d_err);
     delete M;
 }
 

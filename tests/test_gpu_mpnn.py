@@ -1,5 +1,6 @@
-"""The learned restart proposal's CUDA forward/backward against the FP64 oracle,
-its training, and the proposal restart."""
+"""The learned restart proposal's CUDA forward/backward (dense layers on the
+tensor cores) against the FP64 oracle with the same BF16 roundings, its
+training, and the proposal restart."""
 import numpy as np
 import pytest
 
@@ -34,11 +35,23 @@ def test_loss_and_gradient_match_oracle(make):
     net.set_params(p)
     t = np.where(rng.random(inst.n) < 0.5, -1.0, 1.0)
     loss, x0, g = net.loss_grad(h, torch.from_numpy(t.astype(np.float32)).cuda(), want_host_grad=True)
-    lo, go, xo = MO.loss_and_grad(p.astype(np.float64), inst, t, 3, bf16_weights=True)
-    assert abs(float(loss.item()) - lo) <= 1e-5 * max(1.0, abs(lo))
-    assert np.max(np.abs(x0.cpu().numpy() - xo)) < 1e-4
-    scale = np.max(np.abs(go))
-    assert np.all(np.abs(g - go) <= 1e-4 * scale + 1e-3 * np.abs(go)), float(np.max(np.abs(g - go)) / scale)
+    # the oracle with BF16 weights and BF16-rounded dense-product inputs, as the
+    # tensor-core layers compute.  FP32 and FP64 values that fall on opposite
+    # sides of a BF16 rounding boundary differ by one BF16 unit (2^-8 relative),
+    # and such flips propagate through the layers: the bounds below allow a few
+    # BF16 units at the worst element and a fraction of one in RMS (the
+    # unrounded oracle differs by several times more; a wrong operand layout or
+    # a dropped term by the size of the values themselves)
+    lo, go, xo = MO.loss_and_grad(p.astype(np.float64), inst, t, 3, bf16_weights=True, bf16_inputs=True)
+    assert abs(float(loss.item()) - lo) <= 2e-4 * max(1.0, abs(lo))
+    xk = x0.cpu().numpy()
+    assert np.max(np.abs(xk - xo)) < 2e-2 and np.sqrt(np.mean((xk - xo) ** 2)) < 2e-3
+    lay, _ = MO.layout(3)
+    for name, (o, shape) in lay.items():
+        a, b = go[o:o + int(np.prod(shape))], g[o:o + int(np.prod(shape))]
+        scale, rms = np.max(np.abs(a)), np.sqrt(np.mean(a ** 2))
+        assert np.max(np.abs(a - b)) <= 2e-2 * scale, name
+        assert np.sqrt(np.mean((a - b) ** 2)) <= 1e-2 * rms, name
     x1 = net.forward(h)
     assert torch.equal(x1, x0)
 
