@@ -124,12 +124,23 @@ __global__ void __launch_bounds__(TCT) tc_dense_fwd(const float *__restrict__ X1
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r0 = blockIdx.x * TCR;
     tc_setup(&holder, &bar, H);
-    for (int i = tid; i < TCR * kc8; i += TCT) {  // A: 128 rows of [X1, X2]
-        const int r8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
-        const int r = r0 + g * 8 + r8, k = c * 8;
-        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (r < R && k < K) load8(concat_row(X1, K1, X2, K2, r, k), v);
-        tc::st_chunk(As, g, c, kc8, r8, tc::pack8(v));
+    // A: 128 rows of [X1, X2], eight chunks per thread in flight
+    for (int base = tid; base < TCR * kc8; base += 8 * TCT) {
+        float v[8][8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = base + u * TCT;
+            const int r8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
+            const int r = r0 + g * 8 + r8, k = c * 8;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[u][e] = 0.f;
+            if (i < TCR * kc8 && r < R && k < K) load8(concat_row(X1, K1, X2, K2, r, k), v[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = base + u * TCT;
+            if (i < TCR * kc8) tc::st_chunk(As, (i >> 3) / kc8, (i >> 3) % kc8, kc8, i & 7, tc::pack8(v[u]));
+        }
     }
     for (int i = tid; i < H * kc8; i += TCT) {  // B: W, H rows of K
         const int n8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
@@ -182,12 +193,24 @@ __global__ void __launch_bounds__(TCT) tc_dense_bwd_x(const float *__restrict__ 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int r0 = blockIdx.x * TCR;
     tc_setup(&holder, &bar, (uint32_t)N);
-    for (int i = tid; i < TCR * kc8; i += TCT) {  // A: 128 rows of dY
-        const int r8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
-        const int r = r0 + g * 8 + r8;
-        float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        if (r < R) load8(dY + (size_t)r * H + c * 8, v);
-        tc::st_chunk(As, g, c, kc8, r8, tc::pack8(v));
+    // A: 128 rows of dY, eight chunks per thread in flight
+    static_assert(TCR * kc8 == 8 * TCT, "one pass of eight chunks per thread");
+    {
+        float v[8][8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = tid + u * TCT;
+            const int r8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
+            const int r = r0 + g * 8 + r8;
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[u][e] = 0.f;
+            if (r < R) load8(dY + (size_t)r * H + c * 8, v[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = tid + u * TCT;
+            tc::st_chunk(As, (i >> 3) / kc8, (i >> 3) % kc8, kc8, i & 7, tc::pack8(v[u]));
+        }
     }
     for (int i = tid; i < N * kc8; i += TCT) {  // B: W^T, N rows of H (a column of W each)
         const int n8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
@@ -247,39 +270,61 @@ __global__ void __launch_bounds__(TCT) tc_dense_bwd_w(const float *__restrict__ 
         const int k = (i >> 3) / kc8 * 8 + (i & 7);
         if (k >= K) tc::st_chunk(As, (i >> 3) / kc8, (i >> 3) % kc8, kc8, i & 7, make_uint4(0u, 0u, 0u, 0u));
     }
-    // thread t stages B chunks (o = 8 q + (t & 7), rows 8 (t >> 3) .. + 7) for q = 0 .. 7
-    float bsum[H / 8];
-#pragma unroll
-    for (int q = 0; q < H / 8; ++q) bsum[q] = 0.f;
+    // Staging: a task reads 8 consecutive rows x 4 consecutive columns (eight
+    // float4 loads, the lanes of a warp covering consecutive columns of the same
+    // rows) and writes the four transposed chunks (one column, 8 rows each).
+    // B tasks: thread t owns columns o = 4 (t % 16) .. + 3 of dY in every tile.
+    float bsum[4] = {0.f, 0.f, 0.f, 0.f};
     const int tiles = (R + TCR - 1) / TCR;
+    const int K4 = K / 4;
     uint32_t tmem = 0;
     bool ok = true;
     int done = 0;
+    auto stage4 = [&](unsigned char *base, const float *const *rows, int col, int kcol, int rc, float *sum) {
+        float v[8][4];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            if (rows[t]) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(rows[t] + col));
+                v[t][0] = q.x, v[t][1] = q.y, v[t][2] = q.z, v[t][3] = q.w;
+            } else {
+                v[t][0] = v[t][1] = v[t][2] = v[t][3] = 0.f;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            float w[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) w[t] = v[t][c];
+            if (sum)
+#pragma unroll
+                for (int t = 0; t < 8; ++t) sum[c] += w[t];
+            const int k = kcol + c;
+            tc::st_chunk(base, k >> 3, rc, kc8, k & 7, tc::pack8(w));
+        }
+    };
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x, ++done) {
         const int r0 = tile * TCR;
         if (done > 0) ok &= tc::mbar_wait(&bar, (uint32_t)(done - 1) & 1u);  // the MMAs have read the buffers
-        for (int i = tid; i < K * kc8; i += TCT) {  // A[k][r] = X[r][k]
-            const int k8 = i & 7, c = (i >> 3) % kc8, g = (i >> 3) / kc8;
-            const int k = g * 8 + k8;
-            float v[8];
+        for (int i = tid; i < K4 * kc8; i += TCT) {  // A[k][r] = X[r][k]
+            const int j = i % K4, rc = i / K4, k = 4 * j;
+            const float *rows[8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const int r = r0 + c * 8 + t;
-                v[t] = r < R ? __ldg(concat_row(X1, K1, X2, K2, r, k)) : 0.f;
+                const int r = r0 + rc * 8 + t;
+                rows[t] = r < R ? (k < K1 ? X1 + (size_t)r * K1 : X2 + (size_t)r * K2) : nullptr;
             }
-            tc::st_chunk(As, g, c, kc8, k8, tc::pack8(v));
+            stage4(As, rows, k < K1 ? k : k - K1, k, rc, nullptr);
         }
-#pragma unroll
-        for (int q = 0; q < H / 8; ++q) {  // B[o][r] = dY[r][o]
-            const int o8 = tid & 7, c = tid >> 3, o = q * 8 + o8;
-            float v[8];
+        for (int i = tid; i < (H / 4) * kc8; i += TCT) {  // B[o][r] = dY[r][o]
+            const int j = i % (H / 4), rc = i / (H / 4);
+            const float *rows[8];
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const int r = r0 + c * 8 + t;
-                v[t] = r < R ? __ldg(dY + (size_t)r * H + o) : 0.f;
-                bsum[q] += v[t];
+                const int r = r0 + rc * 8 + t;
+                rows[t] = r < R ? dY + (size_t)r * H : nullptr;
             }
-            tc::st_chunk(Bs, q, c, kc8, o8, tc::pack8(v));
+            stage4(Bs, rows, 4 * j, 4 * j, rc, bsum);
         }
         const uint32_t t_addr = tc_publish(&holder);
         tmem = t_addr;
@@ -300,13 +345,13 @@ __global__ void __launch_bounds__(TCT) tc_dense_bwd_w(const float *__restrict__ 
         }
     }
     if (db) {
-        // lanes with equal (lane & 7) hold the same o: fold the warp's four, then one atomic per o
+        // lanes l and l + 16 hold the same columns: fold them, then one atomic per column
+        static_assert(TCT % (H / 4) == 0 && H / 4 == 16, "thread t owns the columns 4 (t % 16) .. + 3");
 #pragma unroll
-        for (int q = 0; q < H / 8; ++q) {
-            float s = bsum[q];
-            s += __shfl_xor_sync(0xffffffffu, s, 8);
+        for (int c = 0; c < 4; ++c) {
+            float s = bsum[c];
             s += __shfl_xor_sync(0xffffffffu, s, 16);
-            if (lane < 8) atomicAdd(db + q * 8 + lane, s);
+            if (lane < 16) atomicAdd(db + 4 * lane + c, s);
         }
     }
     if (!ok && lane == 0) atomicOr(err, 1);
