@@ -144,7 +144,10 @@ typedef struct ffsat_info {
     int32_t tune_pts_per_cta; /* points per CTA of the fused kernel */
     int32_t tune_candidates;  /* candidate images timed at load (0 when the choice came from the cache) */
     int32_t tune_cached;      /* 1 if an earlier instance of the same shape supplied the choice */
-    int32_t pad2;
+    int32_t fix_words_f32;    /* 32-bit words of the FP32 shared-memory-resident fixed-point gradient:
+                                 1 where the weights and degrees allow (each contribution rounded to
+                                 2^-20 of the smallest max(w_c, 1) or finer), else 2; follows
+                                 ffsat_set_weights */
 } ffsat_info;
 
 /* Fill `opt` with the defaults (stable form, closed forms for OR/XOR,

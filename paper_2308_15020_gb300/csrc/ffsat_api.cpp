@@ -160,6 +160,7 @@ struct ffsat_instance {
     double f_const = 0.0;        // constants of the fused kernel's f (see fill_weights)
     double f_const_plain = 0.0;  // sum of w FE over constant constraints
     float fix_s1 = 1.0f, fix_s2 = 1.0f, fix_i1 = 1.0f, fix_i12 = 1.0f;
+    int32_t fix_two = 1;
     double fix64_s = 1.0, fix64_i = 1.0;
     int32_t fix64_l = 0;
     bool fix64_ok = false;  // the cluster step's fixed point resolves 2^-44 or finer
@@ -550,7 +551,9 @@ FusedFn launcher_for(bool f64, int nr) {
 // min(21 - ceil(log2 wmax), 30 - ceil(log2 Dmax)) the hi word is rounded
 // exactly (|c 2^S1| < 2^22) and never exceeds 2^30 in sum (Dmax = largest
 // weighted variable degree); the residual lies in [-1/2, 1/2], so with
-// S2 = min(22, 30 - ceil(log2 degmax)) the lo word is exact and bounded too.
+// S2 = min(22, 30 - ceil(log2 degmax)) the lo word is exact and bounded too
+// (the kernel adds the lo word only where S1 + floor(log2 bmin) < 20, bmin the
+// smallest b_c of a positive weight).
 // The FP64 cluster step rounds each contribution to an integer V = c 2^S64
 // and adds it as two 32-bit words, lo = V mod 2^L and hi = floor(V / 2^L):
 // L = 32 - ceil(log2(degmax + 1)) keeps the lo sums below 2^32, and
@@ -562,11 +565,12 @@ FusedFn launcher_for(bool f64, int nr) {
 void fixed_point_scales(ffsat_instance *I) {
     std::vector<double> D((size_t)I->n, 0.0);
     std::vector<int32_t> deg((size_t)I->n, 0);
-    double wmax = 0.0;
+    double wmax = 0.0, wmin = 0.0;  // over b_c = max(w_c, 1) of the weighted constraints
     for (int32_t c = 0; c < I->m; ++c) {
         if (I->cls[c] == CLS_CONST) continue;
         const double bc = std::max(I->w[c], 1.0);
         wmax = std::max(wmax, bc);
+        if (I->w[c] > 0.0 && (wmin == 0.0 || bc < wmin)) wmin = bc;
         for (int64_t i = I->row_ptr[c]; i < I->row_ptr[c + 1]; ++i) {
             const int32_t l = I->lits_in[i];
             const int32_t v = (l > 0 ? l : -l) - 1;
@@ -590,6 +594,11 @@ void fixed_point_scales(ffsat_instance *I) {
     I->fix_s2 = std::ldexp(1.0f, S2);
     I->fix_i1 = std::ldexp(1.0f, -S1);
     I->fix_i12 = std::ldexp(1.0f, -(S1 + S2));
+    // the hi word alone rounds each contribution to 2^-S1, 2^-(S1 + log2 bmin)
+    // of the smallest bound b_c = max(w_c, 1): enough (FP32 itself rounds sums
+    // to 2^-24) from 2^-20 on.  b_c, not w_c, so that ERWA's weights (which
+    // stay below b_c) keep the choice, and a resumed search with the same bits
+    I->fix_two = (wmin == 0.0 || S1 + (int)std::floor(std::log2(wmin)) >= 20) ? 0 : 1;
     const int L = 32 - (int)std::ceil(std::log2((double)gmax + 1.0));
     const int S64 = std::min(30 + L - e_d, 50 - e_w);
     I->fix64_s = std::ldexp(1.0, S64);
@@ -1428,6 +1437,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     V.fix_s2 = P->fix_s2;
     V.fix_i1 = P->fix_i1;
     V.fix_i12 = P->fix_i12;
+    V.fix_two = P->fix_two;
     V.fix64_s = P->fix64_s;
     V.fix64_i = P->fix64_i;
     V.fix64_l = P->fix64_l;
@@ -1476,6 +1486,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     inf.tune_shape = P->knobs[0].shape;
     inf.tune_clause_k = P->knobs[0].clause_k;
     inf.tune_pts_per_cta = P->knobs[0].pts_per_cta;
+    inf.fix_words_f32 = P->fix_two ? 2 : 1;
     inf.smem_mode_f32 = P->smem_mode32;
     inf.smem_mode_f64 = P->smem_mode64;
     inf.threads_f32 = fused_threads(false, nr32);
@@ -1513,10 +1524,12 @@ int ffsat_set_weights(ffsat_instance *I, const double *weights) {
         W->fix_s2 = I->fix_s2;
         W->fix_i1 = I->fix_i1;
         W->fix_i12 = I->fix_i12;
+        W->fix_two = I->fix_two;
         W->fix64_s = I->fix64_s;
         W->fix64_i = I->fix64_i;
         W->fix64_l = I->fix64_l;
     }
+    I->info.fix_words_f32 = I->fix_two ? 2 : 1;
     return FFSAT_OK;
 }
 

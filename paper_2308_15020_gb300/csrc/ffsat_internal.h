@@ -96,7 +96,7 @@ struct DevView {
     const float4 *tab_im_f;
     const double *tab_im_d;
     int32_t node_form;  // NODE_FORM_IMAG or NODE_FORM_GENERIC: which node task runs
-    int32_t pad2;
+    int32_t fix_two;    // the FP32 fixed-point gradient uses its lo word too (else hi alone)
     // device constants of f under the current weights: [0] = sum over clauses of
     // -w plus sum of w FE over constant constraints (fused kernel), [1] = the
     // latter alone (plain FP64 path); rewritten on the device by the ERWA update

@@ -247,7 +247,12 @@ struct Fix64Acc {
 // integer); every variable receives the same number deg_v of fixed-point
 // contributions in every evaluation, so each word starts the evaluation at
 // bias_v = -deg_v * 0x4B400000 (mod 2^32) and ends it holding the exact sum of
-// the integers (two's-complement sums are exact modulo 2^32).
+// the integers (two's-complement sums are exact modulo 2^32).  The lo word
+// (the residual at 2^-(S1+S2)) is used only where the instance needs it: with
+// unit weights and degrees up to about 2^10 the hi word alone resolves 2^-20,
+// within FP32 rounding of the sums (one shared reduction per contribution).
+// FW = 1: hi only; FW = 2: hi and lo.
+template <int FW>
 struct FixAcc {
     int *hi;
     int *lo;
@@ -258,17 +263,20 @@ struct FixAcc {
         constexpr float kMagic = 12582912.0f;  // 1.5 * 2^23
         const float m1 = __fmaf_rn(c, s1, kMagic);  // c 2^S1 is exact; one rounding to an integer
         const int h = __float_as_int(m1);           // 0x4B400000 + round(c 2^S1)
-        const float r = __fmaf_rn(c, s1, __fsub_rn(kMagic, m1));  // exact residual in [-1/2, 1/2]
-        const float m2 = __fmaf_rn(r, s2, kMagic);
-        const int l = __float_as_int(m2);
         const unsigned a = (unsigned)__cvta_generic_to_shared(hi + v);
-        const unsigned b = (unsigned)__cvta_generic_to_shared(lo + v);
         asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(a), "r"(h) : "memory");
-        asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(b), "r"(l) : "memory");
+        if constexpr (FW == 2) {
+            const float r = __fmaf_rn(c, s1, __fsub_rn(kMagic, m1));  // exact residual in [-1/2, 1/2]
+            const float m2 = __fmaf_rn(r, s2, kMagic);
+            const unsigned b = (unsigned)__cvta_generic_to_shared(lo + v);
+            asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(b), "r"(__float_as_int(m2)) : "memory");
+        }
     }
     __device__ __forceinline__ void addf(uint32_t v, float c) const { atomicAdd(&gf[v], c); }
     __device__ __forceinline__ float get(int v) const {
-        return __fmaf_rn((float)lo[v], i12, __fmaf_rn((float)hi[v], i1, gf[v]));
+        const float g1 = __fmaf_rn((float)hi[v], i1, gf[v]);
+        if constexpr (FW == 2) return __fmaf_rn((float)lo[v], i12, g1);
+        return g1;
     }
     __device__ __forceinline__ void zero(int v) const {
         const int b = bias[v];
@@ -933,7 +941,9 @@ __device__ __forceinline__ double block_sum_all(double v, BlockShared &sh) {
 
 // One point b of one instance: stage x, T projected-GD iterations (or one
 // evaluation), exact check and restart.  All threads of the CTA take part.
-template <typename R, int NR, int NI, int SM, int THREADS>
+// FW: words of the FP32 fixed-point gradient in the shared-memory-resident mode
+// (1 where the instance's range allows it, else 2; see FixAcc).
+template <typename R, int NR, int NI, int SM, int THREADS, int FW = 2>
 __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, int b, unsigned char *smem_raw,
                                           const Src &S, BlockShared &sh) {
     // FP32 node factors: kept in registers between the suffix and the prefix pass,
@@ -948,7 +958,7 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
     // FP32 shared-resident mode: x | g hi words | g lo words | g FP32 words | image;
     // otherwise x | g | image.
     constexpr bool FIX = RES && sizeof(R) == 4;
-    using Acc = typename std::conditional<FIX, FixAcc, PlainAcc<R>>::type;
+    using Acc = typename std::conditional<FIX, FixAcc<FW>, PlainAcc<R>>::type;
     int &s_ctr = sh.ctr;
     double *s_red = sh.red;
     int *s_ired = sh.ired;
@@ -1050,7 +1060,10 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
                     q = block_sum_all(q, sh);
                     const double fp =
                         block_sum_all((double)eval_tasks<R, NR, NI, SF, XG>(V, S, xs, G, false, s_ctr), sh);
-                    if (fp <= fy + d + q / (2.0 * eta) + A.slack) break;  // same value in every thread
+                    // same value in every thread; a trial equal to y (q = 0: every
+                    // coordinate clipped) meets the test with equality and is taken
+                    // without comparing two evaluations of the same point
+                    if (q == 0.0 || fp <= fy + d + q / (2.0 * eta) + A.slack) break;
                     if (ls + 1 < A.maxls) eta *= A.beta;
                 }
                 const double tn = 0.5 * (1.0 + sqrt(1.0 + 4.0 * tk * tk));
@@ -1134,12 +1147,12 @@ constexpr int node_interleave() {
 // ---------------------------------------------------------------------------
 // the fused kernel: one instance, points b = blockIdx.x, blockIdx.x + gridDim.x, ...
 // ---------------------------------------------------------------------------
-template <typename R, int NR, int NI, int SM, int THREADS>
+template <typename R, int NR, int NI, int SM, int THREADS, int FW = 2>
 __global__ void __launch_bounds__(THREADS, 1) fused_kernel(const DevView V, const FusedArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockShared sh;
     const Src S = make_src<R, SM, THREADS>(V, smem_raw, true);
-    for (int b = blockIdx.x; b < A.B; b += gridDim.x) run_point<R, NR, NI, SM, THREADS>(V, A, b, smem_raw, S, sh);
+    for (int b = blockIdx.x; b < A.B; b += gridDim.x) run_point<R, NR, NI, SM, THREADS, FW>(V, A, b, smem_raw, S, sh);
 }
 
 // ---------------------------------------------------------------------------

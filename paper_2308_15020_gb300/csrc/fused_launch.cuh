@@ -38,12 +38,15 @@ cudaError_t raise_smem_limit(Kernel k, size_t smem) {
     return e;
 }
 
-template <typename R, int NR, int SM>
+template <typename R, int NR, int SM, int FW = 2>
 cudaError_t fused_launch_mode(const DevView &V, const FusedArgs &a, size_t smem, int grid, cudaStream_t s,
                               bool prepare_only) {
     constexpr int TH = fused_threads(sizeof(R) == 8, NR);
-    auto k = fused_kernel<R, NR, node_interleave<R, NR>(), SM, TH>;
-    if (prepare_only) return raise_smem_limit(k, smem);
+    auto k = fused_kernel<R, NR, node_interleave<R, NR>(), SM, TH, FW>;
+    // (cached per device and kernel; a weight update can switch an instance to
+    // the other fixed-point variant after its preparation)
+    const cudaError_t e = raise_smem_limit(k, smem);
+    if (prepare_only || e != cudaSuccess) return e;
     k<<<grid, TH, smem, s>>>(V, a);
     return cudaGetLastError();
 }
@@ -55,6 +58,10 @@ cudaError_t fused_launch(const DevView &V, int smem_mode, const FusedArgs &a, si
     case SMEM_FULL:
         return fused_launch_mode<R, NR, SMEM_FULL>(V, a, smem, grid, s, prepare_only);
     case SMEM_RES:
+        // FP32: one fixed-point word where the instance's range allows it
+        if constexpr (sizeof(R) == 4) {
+            if (!V.fix_two) return fused_launch_mode<R, NR, SMEM_RES, 1>(V, a, smem, grid, s, prepare_only);
+        }
         return fused_launch_mode<R, NR, SMEM_RES>(V, a, smem, grid, s, prepare_only);
     case SMEM_X:
         return fused_launch_mode<R, NR, SMEM_X>(V, a, smem, grid, s, prepare_only);

@@ -138,7 +138,7 @@ class Info(C.Structure):
                 ("n_xor2", C.c_int32), ("pad", C.c_int32), ("smem_bytes_f32", C.c_int64),
                 ("smem_bytes_f64", C.c_int64), ("tune_shape", C.c_int32), ("tune_clause_k", C.c_int32),
                 ("tune_pts_per_cta", C.c_int32), ("tune_candidates", C.c_int32), ("tune_cached", C.c_int32),
-                ("pad2", C.c_int32)]
+                ("fix_words_f32", C.c_int32)]
 
     def as_dict(self):
         d = {k: getattr(self, k) for k, _ in self._fields_}

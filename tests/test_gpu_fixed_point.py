@@ -1,0 +1,72 @@
+"""The FP32 shared-memory-resident gradient in one or two fixed-point words:
+the library picks one word where the weights and degrees allow it, two where a
+variable's weighted degree is large, and both variants match the FP64 oracle
+(evaluation and a multi-iteration step)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2308_15020_gb300 import gen
+from parity import compare, to_np
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _hub(n=300, m=5000, seed=3):
+    """Random 3-clauses that all contain variable 1 (weighted degree 5000)."""
+    rng = np.random.default_rng(seed)
+    cons = []
+    for _ in range(m):
+        others = rng.choice(np.arange(2, n + 1), size=2, replace=False)
+        sg = np.where(rng.random(3) < 0.5, -1, 1)
+        cons.append((0, 0, [int(sg[0]), int(sg[1] * others[0]), int(sg[2] * others[1])]))
+    return gen.from_lists(n, cons, name="hub")
+
+
+@pytest.mark.parametrize("name,make,words", [
+    ("cnf_xor", lambda: gen.cnf_xor_2000(7), 1),
+    ("3sat_n100", lambda: gen.uniform_3sat_100(7), 1),
+    ("hub_degree_5000", _hub, 2),
+])
+def test_word_choice_and_parity(name, make, words):
+    from paper_2308_15020_gb300 import ffsat
+
+    inst = make()
+    h = ffsat.Instance(inst)
+    info = h.info()
+    assert info["smem_mode_f32"] == 3 and info["fix_words_f32"] == words
+    B = 16
+    x = gen.uniform_points(B, inst.n, 5)
+    f, g = h.eval_grad(torch.from_numpy(x).cuda())
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+    # ten fixed-step iterations from the same points: within 1e-4 of the FP64 trajectory
+    xs = torch.from_numpy(x.copy()).cuda()
+    h.step(xs, T=10, lr=0.05, seed=1, epoch=1, restart=False)
+    xo, _, _ = O.step(inst, x.astype(np.float64), T=10, lr=0.05, seed=1, epoch=1, restart=False)
+    assert np.max(np.abs(to_np(xs) - xo)) < 1e-4
+
+
+@pytest.mark.parametrize("scale,words", [(1.0, 1), (300.0, 1), ("mixed", 2)])
+def test_weights_switch_word_count(scale, words):
+    """ffsat_set_weights re-derives the scales: uniform weights of any size keep
+    one word; weights spanning 1..300 need the second (a unit-weight clause's
+    contribution would be rounded to 2^-12), and either way the gradient
+    matches the oracle."""
+    from paper_2308_15020_gb300 import ffsat
+
+    inst = gen.uniform_3sat_100(9)
+    h = ffsat.Instance(inst)
+    assert h.info()["fix_words_f32"] == 1
+    if scale == "mixed":
+        w = np.ones(inst.m)
+        w[::7] = 300.0
+    else:
+        w = np.full(inst.m, scale)
+    h.set_weights(w)
+    assert h.info()["fix_words_f32"] == words
+    x = gen.uniform_points(8, inst.n, 2)
+    f, g = h.eval_grad(torch.from_numpy(x).cuda())
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4, weights=w)
+    assert ef <= 1 and eg <= 1, (ef, eg)
