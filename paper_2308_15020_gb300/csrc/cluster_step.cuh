@@ -93,9 +93,11 @@ __device__ __forceinline__ void clause_task_fix(const DevView &V, const Src &S, 
             m1 = fma(flip(wq0, l1), q2, M);
             m2 = fma(flip(wq0, l2), q1, M);
         }
-        if ((l0 & kVarMask) < (uint32_t)n) acc.put(l0 & kVarMask, m0);
-        if ((l1 & kVarMask) < (uint32_t)n) acc.put(l1 & kVarMask, m1);
-        if ((l2 & kVarMask) < (uint32_t)n) acc.put(l2 & kVarMask, m2);
+        // padding literals add into the words of the dummy variables n and n + 1
+        // (both buffers hold npad >= n + 2 words; those words are never read)
+        acc.put(l0 & kVarMask, m0);
+        acc.put(l1 & kVarMask, m1);
+        acc.put(l2 & kVarMask, m2);
     }
 }
 

@@ -204,6 +204,7 @@ __device__ __forceinline__ R gather(const R *xrow, uint32_t lp, int n) {
 // serialise.
 template <typename R>
 struct PlainAcc {
+    static constexpr bool kDummySlots = false;
     R *g;
     __device__ __forceinline__ void add(uint32_t v, R c) const { atomicAdd(&g[v], c); }
     __device__ __forceinline__ void addf(uint32_t v, R c) const { atomicAdd(&g[v], c); }
@@ -222,6 +223,7 @@ struct PlainAcc {
 // 1.5 2^52 + round(a b) and its bit pattern minus that of 1.5 2^52 is the
 // integer.
 struct Fix64Acc {
+    static constexpr bool kDummySlots = false;
     static constexpr double kRound = 6755399441055744.0;  // 1.5 * 2^52
     uint2 *g;  // {lo, hi} per variable
     double s;
@@ -254,6 +256,7 @@ struct Fix64Acc {
 // FW = 1: hi only; FW = 2: hi and lo.
 template <int FW>
 struct FixAcc {
+    static constexpr bool kDummySlots = true;  // npad >= n + 2 words per array
     int *hi;
     int *lo;
     float *gf;
@@ -281,15 +284,21 @@ struct FixAcc {
     __device__ __forceinline__ void zero(int v) const {
         const int b = bias[v];
         hi[v] = b;
-        lo[v] = b;
+        if constexpr (FW == 2) lo[v] = b;
         gf[v] = 0.0f;
     }
 };
 
+// Accumulators whose dummy variables n and n + 1 have words of their own (reset
+// with the others, never read) take the contributions of padding literals
+// there instead of branching around them.
 template <typename R, typename Acc>
 __device__ __forceinline__ void scatter(const Acc &acc, uint32_t lp, R val, int n) {
     const uint32_t v = lp & kVarMask;
-    if (v < (uint32_t)n) acc.add(v, flip(val, lp));
+    if constexpr (Acc::kDummySlots)
+        acc.add(v, flip(val, lp));
+    else if (v < (uint32_t)n)
+        acc.add(v, flip(val, lp));
 }
 
 template <typename R, typename Acc>
