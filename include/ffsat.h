@@ -423,6 +423,14 @@ int32_t ffsat_last_launch_count(void);
  * thread (1 unless it ran one thread-block cluster per point; 0 before any). */
 int32_t ffsat_last_cluster_size(void);
 
+/* Points per CTA of the last ffsat_step / ffsat_step_noalloc call on this
+ * thread: 2 where an FP32 fixed step on the shared-memory-resident image with
+ * one fixed-point word would otherwise need more than one wave of one CTA per SM
+ * and two points' x and gradient words fit beside the image (each warp task then
+ * serves both points with one load of its records; results are those of one
+ * point per CTA bit for bit), else 1; 0 before any. */
+int32_t ffsat_last_points_per_cta(void);
+
 /* Measured fused multiply-add throughput of the current device, for the
  * arithmetic rooflines of a benchmark (the paper has no counterpart).
  * dtype FFSAT_F32 or FFSAT_F64.  Runs independent FMA chains on every SM

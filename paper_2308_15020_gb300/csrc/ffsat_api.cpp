@@ -26,6 +26,7 @@ namespace {
 thread_local std::string t_err;
 thread_local int32_t t_launches = 0;
 thread_local int32_t t_cluster = 0;
+thread_local int32_t t_pairs = 0;
 
 int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -1178,6 +1179,8 @@ int32_t ffsat_last_launch_count(void) { return t_launches; }
 
 int32_t ffsat_last_cluster_size(void) { return t_cluster; }
 
+int32_t ffsat_last_points_per_cta(void) { return t_pairs; }
+
 int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, const int32_t *lits,
                         const uint8_t *type, const int32_t *param, const double *weights,
                         const ffsat_options *opt_in, ffsat_instance **out) {
@@ -1585,18 +1588,43 @@ static int step_cluster_size(ffsat_instance *I, int32_t B, int mode, size_t &sme
     return 1;
 }
 
+// Dynamic shared memory of the two-points-per-CTA step: the one-point layout
+// (x | hi | lo | gf | image) plus the second point's x | hi | gf.
+static size_t pair_smem(const ffsat_instance *I) {
+    const size_t npad = ((size_t)I->n + 2 + 3) & ~size_t(3);
+    return I->smem32 + 3 * npad * 4;
+}
+
+// Two points per CTA for an FP32 fixed step on the resident image with one
+// fixed-point word, where the points would otherwise need more than one wave
+// of one CTA per SM and the second point's words fit beside the image: each
+// warp task then serves both points with one load of its records.
+static bool step_pairs(const ffsat_instance *I, bool f64, int mode, const FusedArgs &a, int32_t B) {
+    return !f64 && mode == SMEM_RES && !I->fix_two && a.mode == MODE_STEP && B > I->num_sms &&
+           std::max(1, I->knobs[0].pts_per_cta) == 1 && pair_smem(I) + 1024 <= (size_t)I->max_smem;
+}
+
 // The fused step launch of ffsat_step and ffsat_step_noalloc.
 static int launch_step(ffsat_instance *I, bool f64, int mode, const FusedArgs &a, int32_t B, void *stream) {
     const DevView &V = f64 ? I->V64 : I->V32;
     size_t csmem = 0, g1_off = 0;
     const int cl = f64 ? step_cluster_size(I, B, mode, csmem, g1_off) : 1;
-    if (cl > 1)
+    bool pairs = false;
+    if (cl > 1) {
         CUDA_TRY(cluster_launcher(I->nr64)(V, mode, a, csmem, g1_off, B, cl, static_cast<cudaStream_t>(stream),
                                            nullptr));
-    else
+    } else if ((pairs = step_pairs(I, f64, mode, a, B))) {
+        // two points per CTA: the second point's x and gradient words after the image
+        FusedArgs ap = a;
+        ap.pairs = 1;
+        CUDA_TRY(launcher_for(false, I->nr32)(V, mode, ap, pair_smem(I), (B + 1) / 2, static_cast<cudaStream_t>(stream),
+                                              false));
+    } else {
         CUDA_TRY(launcher_for(f64, f64 ? I->nr64 : I->nr32)(V, mode, a, f64 ? I->smem64 : I->smem32, grid_for(I, f64, B),
                                                               static_cast<cudaStream_t>(stream), false));
+    }
     t_cluster = cl;
+    t_pairs = pairs ? 2 : 1;
     t_launches = 1;
     return FFSAT_OK;
 }
@@ -1649,6 +1677,7 @@ int ffsat_step(ffsat_instance *I, int32_t B, void *x, int32_t dtype, const ffsat
     t_err.clear();
     t_launches = 0;
     t_cluster = 1;
+    t_pairs = 1;
     if (!I || !args) return fail(FFSAT_ERR_ARG, "NULL argument");
     if (B < 0 || args->T < 0) return fail(FFSAT_ERR_ARG, "B and T must be >= 0");
     if (!std::isfinite(args->lr)) return fail(FFSAT_ERR_ARG, "lr must be finite");
@@ -1696,6 +1725,7 @@ int ffsat_step_noalloc(ffsat_instance *I, int32_t B, void *x, int32_t dtype, con
     t_err.clear();
     t_launches = 0;
     t_cluster = 1;
+    t_pairs = 1;
     if (!I || !args) return fail(FFSAT_ERR_ARG, "NULL argument");
     if (B < 0 || args->T < 0) return fail(FFSAT_ERR_ARG, "B and T must be >= 0");
     if (!std::isfinite(args->lr)) return fail(FFSAT_ERR_ARG, "lr must be finite");

@@ -160,7 +160,7 @@ struct FusedArgs {
     // optional per-point outputs (iterations taken, final step size)
     double beta, eta_min, slack;
     int32_t maxls;
-    int32_t pad2;
+    int32_t pairs;  // MODE_STEP: two points per CTA (FP32 resident image, one fixed-point word)
     void *y_scratch;
     int32_t *iters;
     double *eta_out;

@@ -1145,6 +1145,174 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Two points per CTA (fixed step, FP32, shared-memory-resident image, one
+// fixed-point word): every warp task is evaluated at both points after one
+// load of its clause records, which shares the record loads and the task
+// overhead and gives each warp two independent dependency chains.  Point 0
+// keeps the one-point layout (x | hi | lo (unused) | gf | image); point 1 has
+// its own x | hi | gf block after the image.  Each point's arithmetic is the
+// one-point kernel's, term for term, and its fixed-point sums do not depend on
+// the order of the reductions, so both points end with the one-point results
+// bit for bit.
+// ---------------------------------------------------------------------------
+template <int CPL, bool XOR>
+__device__ __forceinline__ void clause_task2(const DevView &V, const Src &S, int4 task, int lane, const float *x0,
+                                             const float *x1, const FixAcc<1> &G0, const FixAcc<1> &G1) {
+    const int n = V.n;
+    int4 cl[CPL];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) cl[k] = S.clauses[task.y + k * 32 + lane];
+#pragma unroll
+    for (int k = 0; k < CPL; ++k) {
+        const float w = clause_weight<float>(V, cl[k], task.y + k * 32 + lane);
+        const uint32_t l0 = (uint32_t)cl[k].x, l1 = (uint32_t)cl[k].y, l2 = (uint32_t)cl[k].z;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float *xr = p ? x1 : x0;
+            const FixAcc<1> &G = p ? G1 : G0;
+            const float y0 = gather<float, SMEM_FULL>(xr, l0, n);
+            const float y1 = gather<float, SMEM_FULL>(xr, l1, n);
+            const float y2 = gather<float, SMEM_FULL>(xr, l2, n);
+            if constexpr (XOR) {
+                const float wy2 = w * y2;
+                const float y01 = y0 * y1;
+                scatter<float>(G, l0, wy2 * y1, n);
+                scatter<float>(G, l1, wy2 * y0, n);
+                scatter<float>(G, l2, w * y01, n);
+            } else {
+                const float q0 = 0.5f + 0.5f * y0;
+                const float q1 = 0.5f + 0.5f * y1;
+                const float q2 = 0.5f + 0.5f * y2;
+                const float wq12 = w * (q1 * q2);
+                const float wq0 = w * q0;
+                scatter<float>(G, l0, wq12, n);
+                scatter<float>(G, l1, wq0 * q2, n);
+                scatter<float>(G, l2, wq0 * q1, n);
+            }
+        }
+    }
+}
+
+// One evaluation (gradients only) of every warp task at both points; starts and
+// ends with a CTA barrier.
+template <int NR, int NI, bool SF>
+__device__ __forceinline__ void eval_tasks2(const DevView &V, const Src &S, const float *x0, const float *x1,
+                                            const FixAcc<1> &G0, const FixAcc<1> &G1, int &s_ctr) {
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) s_ctr = 0;
+    __syncthreads();
+    float facc = 0.0f;  // the objective is not needed by a fixed step
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&s_ctr, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= V.n_task) break;
+        const int4 task = S.tasks[t];
+        const int kind = task.x & 0xff;
+        if (kind == TASK_CLAUSE || kind == TASK_XOR2) {
+            const bool xr = kind == TASK_XOR2;
+            if (task.z == 128) {
+                if (xr) clause_task2<4, true>(V, S, task, lane, x0, x1, G0, G1);
+                else clause_task2<4, false>(V, S, task, lane, x0, x1, G0, G1);
+            } else if (task.z == 64) {
+                if (xr) clause_task2<2, true>(V, S, task, lane, x0, x1, G0, G1);
+                else clause_task2<2, false>(V, S, task, lane, x0, x1, G0, G1);
+            } else {
+                if (xr) clause_task2<1, true>(V, S, task, lane, x0, x1, G0, G1);
+                else clause_task2<1, false>(V, S, task, lane, x0, x1, G0, G1);
+            }
+        } else if (kind == TASK_PROD) {
+            prod_task<float, SMEM_FULL>(V, S, task, lane, x0, G0, true, facc);
+            prod_task<float, SMEM_FULL>(V, S, task, lane, x1, G1, true, facc);
+        } else {
+            node_dispatch<float, NR, NI, SF, SMEM_FULL>(V, S, task, lane, x0, G0, true, facc, false);
+            node_dispatch<float, NR, NI, SF, SMEM_FULL>(V, S, task, lane, x1, G1, true, facc, false);
+        }
+    }
+    __syncthreads();
+}
+
+// Points b and b + 1 through T fixed-step iterations, the exact check, the
+// violation counts, the restart and the write-back, as run_point does for one.
+template <int NR, int NI, int THREADS>
+__device__ __forceinline__ void run_pair(const DevView &V, const FusedArgs &A, int b, unsigned char *smem_raw,
+                                         const Src &S, BlockShared &sh) {
+    constexpr bool SF = !(NR >= 16 && THREADS > 384);  // as run_point for FP32
+    const int n = V.n;
+    const int npad = (n + 2 + 3) & ~3;
+    const int tid = threadIdx.x;
+    unsigned char *blk1 = smem_raw + image_offset<float, SMEM_RES>(n) + (size_t)V.res_int4 * 16;
+    float *xs[2] = {reinterpret_cast<float *>(smem_raw), reinterpret_cast<float *>(blk1)};
+    FixAcc<1> G[2];
+    G[0].hi = reinterpret_cast<int *>(smem_raw + (size_t)npad * 4);
+    G[0].lo = G[0].hi + npad;
+    G[0].gf = reinterpret_cast<float *>(G[0].lo + npad);
+    G[1].hi = reinterpret_cast<int *>(blk1 + (size_t)npad * 4);
+    G[1].lo = nullptr;
+    G[1].gf = reinterpret_cast<float *>(G[1].hi + npad);
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        G[p].bias = V.fix_bias;
+        G[p].s1 = V.fix_s1;
+        G[p].s2 = V.fix_s2;
+        G[p].i1 = V.fix_i1;
+        G[p].i12 = V.fix_i12;
+    }
+    const float *x_in = static_cast<const float *>(A.x_in);
+    float *x_out = static_cast<float *>(A.x_out);
+    const float lr = float(A.sp.lr);
+    bool bad = false;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const size_t rowoff = (size_t)(b + p) * (size_t)n;
+        for (int v = tid; v < n; v += THREADS) {
+            const float xv = x_in[rowoff + v];
+            bad |= isnan(xv);
+            xs[p][v] = xv;
+        }
+        if (tid == 0) {
+            xs[p][n] = 1.0f;
+            xs[p][n + 1] = 0.0f;
+        }
+        for (int v = tid; v < npad; v += THREADS) G[p].zero(v);
+    }
+    if (bad) atomicOr(V.status, STATUS_NAN);
+    for (int it = 0; it < A.sp.T; ++it) {
+        eval_tasks2<NR, NI, SF>(V, S, xs[0], xs[1], G[0], G[1], sh.ctr);
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            for (int v = tid; v < n; v += THREADS) {
+                float z = xs[p][v] - lr * G[p].get(v);
+                z = z < -1.0f ? -1.0f : (z > 1.0f ? 1.0f : z);
+                xs[p][v] = z;
+                G[p].zero(v);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+        const int unsat = block_unsat<float>(V, xs[p], sh.ired, A.unsat_counts);
+        if (tid == 0) sh.ired[0] = unsat;
+        __syncthreads();
+        const int u = sh.ired[0];
+        __syncthreads();  // every thread has read u before the next check writes sh.ired
+        if (tid == 0) {
+            if (A.solved) A.solved[b + p] = (uint8_t)(u == 0);
+            if (A.n_unsat) A.n_unsat[b + p] = u;
+        }
+        if (u != 0 && A.sp.restart) {
+            const uint64_t kb = splitmix64(splitmix64(splitmix64(A.sp.seed) ^ A.sp.epoch) ^
+                                           (A.sp.b_offset + (uint64_t)(b + p)));
+            for (int v = tid; v < n; v += THREADS) xs[p][v] = restart_value<float>(kb, (uint64_t)v);
+        }
+        const size_t rowoff = (size_t)(b + p) * (size_t)n;
+        for (int v = tid; v < n; v += THREADS) x_out[rowoff + v] = xs[p][v];
+    }
+    __syncthreads();
+}
+
 // Nodes per iteration of the node loop (independent multiply chains): one.  Two
 // interleaved nodes at 16 literals per lane need about 170 registers and were
 // measured slower on the cardinality workload (fewer warps per SM).
@@ -1156,12 +1324,23 @@ constexpr int node_interleave() {
 // ---------------------------------------------------------------------------
 // the fused kernel: one instance, points b = blockIdx.x, blockIdx.x + gridDim.x, ...
 // ---------------------------------------------------------------------------
-template <typename R, int NR, int NI, int SM, int THREADS, int FW = 2>
+// PP = 2: two points per CTA (fixed step, FP32, SMEM_RES, FW = 1; run_pair),
+// the last point of an odd B alone.
+template <typename R, int NR, int NI, int SM, int THREADS, int FW = 2, int PP = 1>
 __global__ void __launch_bounds__(THREADS, 1) fused_kernel(const DevView V, const FusedArgs A) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ BlockShared sh;
     const Src S = make_src<R, SM, THREADS>(V, smem_raw, true);
-    for (int b = blockIdx.x; b < A.B; b += gridDim.x) run_point<R, NR, NI, SM, THREADS, FW>(V, A, b, smem_raw, S, sh);
+    if constexpr (PP == 2) {
+        static_assert(sizeof(R) == 4 && SM == SMEM_RES && FW == 1, "two points per CTA: FP32, resident, one word");
+        for (int b = 2 * blockIdx.x; b < A.B; b += 2 * gridDim.x) {
+            if (b + 1 < A.B) run_pair<NR, NI, THREADS>(V, A, b, smem_raw, S, sh);
+            else run_point<R, NR, NI, SM, THREADS, FW>(V, A, b, smem_raw, S, sh);
+        }
+    } else {
+        for (int b = blockIdx.x; b < A.B; b += gridDim.x)
+            run_point<R, NR, NI, SM, THREADS, FW>(V, A, b, smem_raw, S, sh);
+    }
 }
 
 // ---------------------------------------------------------------------------

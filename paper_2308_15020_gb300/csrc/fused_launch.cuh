@@ -38,11 +38,11 @@ cudaError_t raise_smem_limit(Kernel k, size_t smem) {
     return e;
 }
 
-template <typename R, int NR, int SM, int FW = 2>
+template <typename R, int NR, int SM, int FW = 2, int PP = 1>
 cudaError_t fused_launch_mode(const DevView &V, const FusedArgs &a, size_t smem, int grid, cudaStream_t s,
                               bool prepare_only) {
     constexpr int TH = fused_threads(sizeof(R) == 8, NR);
-    auto k = fused_kernel<R, NR, node_interleave<R, NR>(), SM, TH, FW>;
+    auto k = fused_kernel<R, NR, node_interleave<R, NR>(), SM, TH, FW, PP>;
     // (cached per device and kernel; a weight update can switch an instance to
     // the other fixed-point variant after its preparation)
     const cudaError_t e = raise_smem_limit(k, smem);
@@ -60,6 +60,9 @@ cudaError_t fused_launch(const DevView &V, int smem_mode, const FusedArgs &a, si
     case SMEM_RES:
         // FP32: one fixed-point word where the instance's range allows it
         if constexpr (sizeof(R) == 4) {
+            // two points per CTA where the caller asks for them (smem and grid sized for it)
+            if (!V.fix_two && a.pairs)
+                return fused_launch_mode<R, NR, SMEM_RES, 1, 2>(V, a, smem, grid, s, prepare_only);
             if (!V.fix_two) return fused_launch_mode<R, NR, SMEM_RES, 1>(V, a, smem, grid, s, prepare_only);
         }
         return fused_launch_mode<R, NR, SMEM_RES>(V, a, smem, grid, s, prepare_only);

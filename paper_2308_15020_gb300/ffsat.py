@@ -72,6 +72,7 @@ SYMBOLS = (
     "ffsat_instance_info",
     "ffsat_last_launch_count",
     "ffsat_last_cluster_size",
+    "ffsat_last_points_per_cta",
     "ffsat_alu_peak",
     "ffsat_last_error",
     "ffsat_free",
@@ -230,6 +231,8 @@ def lib():
         L.ffsat_last_launch_count.restype = C.c_int32
         L.ffsat_last_cluster_size.argtypes = []
         L.ffsat_last_cluster_size.restype = C.c_int32
+        L.ffsat_last_points_per_cta.argtypes = []
+        L.ffsat_last_points_per_cta.restype = C.c_int32
         L.ffsat_last_error.argtypes = []
         L.ffsat_last_error.restype = C.c_char_p
         L.ffsat_free.argtypes = [_vp]
@@ -250,6 +253,11 @@ def last_launch_count() -> int:
 def last_cluster_size() -> int:
     """CTAs per point of the last step call on this thread (1: one CTA per point)."""
     return int(lib().ffsat_last_cluster_size())
+
+
+def last_points_per_cta() -> int:
+    """Points per CTA of the last step call on this thread (2: two points per CTA)."""
+    return int(lib().ffsat_last_points_per_cta())
 
 
 def alu_peak(dtype: int = FFSAT_F32, target_ms: float = 50.0, stream=None):

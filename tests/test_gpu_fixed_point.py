@@ -70,3 +70,32 @@ def test_weights_switch_word_count(scale, words):
     f, g = h.eval_grad(torch.from_numpy(x).cuda())
     ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4, weights=w)
     assert ef <= 1 and eg <= 1, (ef, eg)
+
+
+@pytest.mark.parametrize("B", [305, 400])
+def test_two_points_per_cta_equal_one_point_per_cta(B):
+    """Enough points for two per CTA: the paired launch (an odd B leaves the last
+    point alone) gives the one-point-per-CTA results bit for bit (points, flags,
+    violation counts, restarts), the latter run in chunks of at most one wave."""
+    from paper_2308_15020_gb300 import ffsat
+
+    inst = gen.cnf_xor_2000(12)
+    h = ffsat.Instance(inst)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    x0 = gen.uniform_points(B, inst.n, 8)
+    xa = torch.from_numpy(x0.copy()).cuda()
+    Ua = torch.zeros(inst.m, dtype=torch.int32, device="cuda")
+    sa, na = h.step(xa, T=30, lr=0.1, seed=2, epoch=3, restart=True, unsat_counts=Ua)
+    assert ffsat.last_points_per_cta() == 2
+    xb = torch.from_numpy(x0.copy()).cuda()
+    Ub = torch.zeros(inst.m, dtype=torch.int32, device="cuda")
+    sb, nb = [], []
+    for s in range(0, B, sms):
+        part = xb[s:s + sms]
+        ss, nn = h.step(part, T=30, lr=0.1, seed=2, epoch=3, restart=True, b_offset=s, unsat_counts=Ub)
+        assert ffsat.last_points_per_cta() == 1
+        sb.append(to_np(ss))
+        nb.append(to_np(nn))
+    assert torch.equal(xa, xb)
+    assert np.array_equal(to_np(sa), np.concatenate(sb)) and np.array_equal(to_np(na), np.concatenate(nb))
+    assert torch.equal(Ua, Ub)
