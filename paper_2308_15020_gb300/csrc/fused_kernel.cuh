@@ -1123,6 +1123,7 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
         }
     }
     if (step) {
+        __syncthreads();  // the staged x (T = 0) or the last update is complete
         const R *xc = (XG != SMEM_NONE) ? xs : (x_out + rowoff);
         const int unsat = block_unsat<R>(V, xc, s_ired, A.unsat_counts);
         if (tid == 0) s_ired[0] = unsat;
@@ -1291,6 +1292,7 @@ __device__ __forceinline__ void run_pair(const DevView &V, const FusedArgs &A, i
         }
         __syncthreads();
     }
+    __syncthreads();  // the staged points (T = 0) are complete
 #pragma unroll
     for (int p = 0; p < 2; ++p) {
         const int unsat = block_unsat<float>(V, xs[p], sh.ired, A.unsat_counts);
