@@ -99,3 +99,35 @@ def test_two_points_per_cta_equal_one_point_per_cta(B):
     assert torch.equal(xa, xb)
     assert np.array_equal(to_np(sa), np.concatenate(sb)) and np.array_equal(to_np(na), np.concatenate(nb))
     assert torch.equal(Ua, Ub)
+
+
+def test_two_points_per_cta_through_noalloc_and_graph():
+    """The allocation-free entry point and a captured CUDA graph take the paired
+    launch too, with the same bits as the ordinary call."""
+    from paper_2308_15020_gb300 import ffsat
+
+    inst = gen.cnf_xor_2000(13)
+    h = ffsat.Instance(inst)
+    B = 320
+    x0 = torch.from_numpy(gen.uniform_points(B, inst.n, 9)).cuda()
+    xa = x0.clone()
+    h.step(xa, T=15, lr=0.1, seed=5, epoch=1)
+    assert ffsat.last_points_per_cta() == 2
+    xb = x0.clone()
+    h.step_noalloc(xb, T=15, lr=0.1, seed=5, epoch=1)
+    assert ffsat.last_points_per_cta() == 2
+    assert torch.equal(xa, xb)
+    xg = x0.clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        h.step(xg.clone(), T=15, lr=0.1, seed=5, epoch=1)  # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        h.step(xg, T=15, lr=0.1, seed=5, epoch=1)
+    xg.copy_(x0)
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(xa, xg)
