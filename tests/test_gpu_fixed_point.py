@@ -70,6 +70,11 @@ def test_weights_switch_word_count(scale, words):
     f, g = h.eval_grad(torch.from_numpy(x).cuda())
     ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-4, weights=w)
     assert ef <= 1 and eg <= 1, (ef, eg)
+    # a step with more points than SMs pairs them only with one fixed-point word
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    xs = torch.from_numpy(gen.uniform_points(sms + 9, inst.n, 3)).cuda()
+    h.step(xs, T=2, lr=0.05, seed=1, epoch=1, restart=False)
+    assert ffsat.last_points_per_cta() == (2 if words == 1 else 1)
 
 
 @pytest.mark.parametrize("B", [305, 400])
