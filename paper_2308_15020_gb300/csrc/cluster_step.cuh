@@ -200,6 +200,7 @@ __global__ void __launch_bounds__(THREADS, 1) fused_cluster_kernel(const DevView
     const int fl = V.fix64_l;
     Fix64Acc G;
     G.s = V.fix64_s;
+    G.inv = V.fix64_i;
     G.l = fl;
     for (int it = 0; it < A.sp.T; ++it) {
         U *const gw = (it & 1) ? g1 : g0;

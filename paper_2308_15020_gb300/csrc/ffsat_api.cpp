@@ -960,6 +960,20 @@ int upload_image(ffsat_instance *P, int k) {
     return FFSAT_OK;
 }
 
+// FP64 shared-memory mode: the gradient in shared memory is the two-word fixed
+// point (Fix64Acc); where its resolution would be coarser than 2^-44 (very high
+// degrees or weights) the instance keeps the gradient in a global row instead
+// (SMEM_X, native FP64 global atomics).
+void fp64_mode(ffsat_instance *P) {
+    P->smem_mode64 = smem_mode_for(P->n, sizeof(double), P->image[1].size() * sizeof(int4), P->max_smem, P->smem64);
+    if (!P->fix64_ok && (P->smem_mode64 == SMEM_FULL || P->smem_mode64 == SMEM_RES)) {
+        P->smem_mode64 = SMEM_X;
+        P->smem64 = (((size_t)P->n + 2 + 3) & ~size_t(3)) * sizeof(double);
+    }
+    P->info.smem_mode_f64 = P->smem_mode64;
+    P->info.smem_bytes_f64 = (int64_t)P->smem64;
+}
+
 // Tile choices found by earlier loads, keyed by the instance's shape (sizes,
 // path counts, longest node constraint, node work, form): an instance of the
 // same shape reuses them without timing.
@@ -1462,7 +1476,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     P->nr64 = nr64;
 
     P->smem_mode32 = smem_mode_for(n_vars, sizeof(float), P->image[0].size() * sizeof(int4), P->max_smem, P->smem32);
-    P->smem_mode64 = smem_mode_for(n_vars, sizeof(double), P->image[1].size() * sizeof(int4), P->max_smem, P->smem64);
+    fp64_mode(P);
     FusedArgs dummy{};
     CUDA_TRY(launcher_for(false, nr32)(P->V32, P->smem_mode32, dummy, P->smem32, 0, 0, true));
     CUDA_TRY(launcher_for(true, nr64)(P->V64, P->smem_mode64, dummy, P->smem64, 0, 0, true));
@@ -1533,6 +1547,7 @@ int ffsat_set_weights(ffsat_instance *I, const double *weights) {
         W->fix64_l = I->fix64_l;
     }
     I->info.fix_words_f32 = I->fix_two ? 2 : 1;
+    fp64_mode(I);  // the fixed point's resolution follows the weights
     return FFSAT_OK;
 }
 

@@ -223,10 +223,10 @@ struct PlainAcc {
 // 1.5 2^52 + round(a b) and its bit pattern minus that of 1.5 2^52 is the
 // integer.
 struct Fix64Acc {
-    static constexpr bool kDummySlots = false;
+    static constexpr bool kDummySlots = true;  // npad >= n + 2 words
     static constexpr double kRound = 6755399441055744.0;  // 1.5 * 2^52
     uint2 *g;  // {lo, hi} per variable
-    double s;
+    double s, inv;  // 2^S64 and 2^-S64
     int l;
     // m = fma(a, b, kRound): adds round(a b) to variable v
     __device__ __forceinline__ void put(uint32_t v, double m) const {
@@ -239,6 +239,13 @@ struct Fix64Acc {
     }
     __device__ __forceinline__ void add(uint32_t v, double c) const { put(v, fma(c, s, kRound)); }
     __device__ __forceinline__ void addf(uint32_t v, double c) const { add(v, c); }
+    // g = (hi 2^L + lo) 2^-S64
+    __device__ __forceinline__ double get(int v) const {
+        const uint2 w = g[v];
+        const long long G = (long long)((unsigned long long)(long long)(int)w.y << l) + (long long)w.x;
+        return (double)G * inv;
+    }
+    __device__ __forceinline__ void zero(int v) const { g[v] = make_uint2(0u, 0u); }
 };
 
 // Clause and node contributions (bounded by their weight) go to the fixed-point
@@ -967,7 +974,12 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
     // FP32 shared-resident mode: x | g hi words | g lo words | g FP32 words | image;
     // otherwise x | g | image.
     constexpr bool FIX = RES && sizeof(R) == 4;
-    using Acc = typename std::conditional<FIX, FixAcc<FW>, PlainAcc<R>>::type;
+    // FP64 with the gradient in shared memory: two-word fixed point (Fix64Acc;
+    // the host keeps such instances out of these modes where its resolution
+    // would be coarser than 2^-44)
+    constexpr bool FIX64 = sizeof(R) == 8 && XG == SMEM_FULL;
+    using Acc = typename std::conditional<FIX, FixAcc<FW>,
+                                          typename std::conditional<FIX64, Fix64Acc, PlainAcc<R>>::type>::type;
     int &s_ctr = sh.ctr;
     double *s_red = sh.red;
     int *s_ired = sh.ired;
@@ -1023,6 +1035,13 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
         G.s2 = V.fix_s2;
         G.i1 = V.fix_i1;
         G.i12 = V.fix_i12;
+        want_g = step || g_out != nullptr;
+        glen = npad;
+    } else if constexpr (FIX64) {
+        G.g = reinterpret_cast<uint2 *>(gs);
+        G.s = V.fix64_s;
+        G.inv = V.fix64_i;
+        G.l = V.fix64_l;
         want_g = step || g_out != nullptr;
         glen = npad;
     } else if constexpr (XG == SMEM_FULL) {

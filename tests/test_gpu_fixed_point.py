@@ -136,3 +136,36 @@ def test_two_points_per_cta_through_noalloc_and_graph():
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(xa, xg)
+
+
+@pytest.mark.parametrize("name,make,mode", [
+    ("3sat_n100", lambda: gen.uniform_3sat_100(4), 3),
+    ("cnf_xor_300", lambda: gen.cnf_xor_2000(6, n=300), 3),
+    ("hub_degree_5000", _hub, 1),  # the fixed point would resolve only 2^-36: gradient in a global row
+])
+def test_fp64_fixed_point_eval_and_step(name, make, mode):
+    """FP64 with the gradient in shared memory accumulates it in two-word fixed
+    point: within 1e-10 of the oracle, and repeated calls give the same bits; an
+    instance whose range would make it coarser keeps FP64 atomics in global rows."""
+    from paper_2308_15020_gb300 import ffsat
+
+    inst = make()
+    h = ffsat.Instance(inst, cluster=1)
+    assert h.info()["smem_mode_f64"] == mode
+    x = gen.uniform_points(12, inst.n, 7, dtype=np.float64)
+    outs = []
+    for _ in range(2):
+        f, g = h.eval_grad(torch.from_numpy(x).cuda())
+        outs.append((to_np(f), to_np(g)))
+    ef, eg = compare(inst, x, outs[0][0], outs[0][1], 1e-10)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+    if mode == 3:
+        assert np.array_equal(outs[0][1].view(np.uint64), outs[1][1].view(np.uint64))
+    xa = torch.from_numpy(x.copy()).cuda()
+    xb = torch.from_numpy(x.copy()).cuda()
+    h.step(xa, T=20, lr=0.05, seed=1, epoch=1, restart=False)
+    h.step(xb, T=20, lr=0.05, seed=1, epoch=1, restart=False)
+    xo, _, _ = O.step(inst, x, T=20, lr=0.05, seed=1, epoch=1, restart=False)
+    assert np.max(np.abs(to_np(xa) - xo)) < 1e-9
+    if mode == 3:
+        assert torch.equal(xa, xb)
