@@ -428,7 +428,8 @@ int32_t ffsat_last_cluster_size(void);
  * one fixed-point word would otherwise need more than one wave of one CTA per SM
  * and two points' x and gradient words fit beside the image (each warp task then
  * serves both points with one load of its records; results are those of one
- * point per CTA bit for bit), else 1; 0 before any. */
+ * point per CTA, bit for bit where every contribution is fixed point, to FP32
+ * rounding where XOR products add with FP32 atomics), else 1; 0 before any. */
 int32_t ffsat_last_points_per_cta(void);
 
 /* Measured fused multiply-add throughput of the current device, for the

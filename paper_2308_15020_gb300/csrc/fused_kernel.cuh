@@ -1174,7 +1174,8 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
 // its own x | hi | gf block after the image.  Each point's arithmetic is the
 // one-point kernel's, term for term, and its fixed-point sums do not depend on
 // the order of the reductions, so both points end with the one-point results
-// bit for bit.
+// bit for bit where every contribution is fixed point (XOR products add with
+// FP32 atomics, whose order may differ).
 // ---------------------------------------------------------------------------
 template <int CPL, bool XOR>
 __device__ __forceinline__ void clause_task2(const DevView &V, const Src &S, int4 task, int lane, const float *x0,
