@@ -6,14 +6,16 @@
 //
 //   * every CTA holds the point's x in its shared memory and evaluates the warp
 //     tasks r, r + CL, r + 2 CL, ... (r = its rank in the cluster) into its own
-//     gradient buffer, in fixed point (Fix64Acc: two native 32-bit
-//     shared-memory reductions per contribution, no compare-and-swap loops);
+//     gradient buffer: clause and node contributions in fixed point (Fix64Acc:
+//     two native 32-bit shared-memory reductions each, no compare-and-swap
+//     loops), product contributions in an FP64 word per variable (atomicAdd);
 //   * the cluster barrier (release / acquire) makes the CL partial gradients
 //     visible to the whole cluster;
 //   * every CTA sums the CL partials of each variable through distributed
 //     shared memory and takes the same step x <- clip(x - lr g, -1, 1) on its
 //     own copy, so the copies stay identical.  Integer sums do not depend on
-//     the order of the additions: the step is bit-reproducible.
+//     the order of the additions: without product constraints the step is
+//     bit-reproducible.
 //
 // Two gradient buffers alternate between iterations: the buffer a CTA clears
 // after the barrier of iteration k was last read by its peers before that
@@ -50,6 +52,14 @@ __device__ __forceinline__ void cluster_barrier() {
 }
 
 // Element v of the shared array `local` as held by CTA `rank` of the cluster.
+__device__ __forceinline__ double ld_peer(const double *local, int v, int rank) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(local + v);
+    uint32_t ra;
+    double x;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(x) : "r"(ra) : "memory");
+    return x;
+}
 __device__ __forceinline__ uint2 ld_peer(const uint2 *local, int v, int rank) {
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(local + v);
     uint32_t ra;
@@ -173,8 +183,12 @@ __global__ void __launch_bounds__(THREADS, 1) fused_cluster_kernel(const DevView
     const int tid = threadIdx.x;
     R *xs = reinterpret_cast<R *>(smem_raw);
     using U = uint2;
+    // fixed-point words, then the FP64 product words (Fix64Acc::addf)
     U *const g0 = reinterpret_cast<U *>(xs + npad);
     U *const g1 = reinterpret_cast<U *>(smem_raw + g1_off);
+    R *const gf0 = reinterpret_cast<R *>(g0 + npad);
+    R *const gf1 = reinterpret_cast<R *>(g1 + npad);
+    const bool prods = V.has_prod != 0;  // only product tasks add to the FP64 words
     const R *x_in = static_cast<const R *>(A.x_in);
     R *x_out = static_cast<R *>(A.x_out);
     const size_t rowoff = (size_t)b * (size_t)n;
@@ -192,6 +206,8 @@ __global__ void __launch_bounds__(THREADS, 1) fused_cluster_kernel(const DevView
     for (int v = tid; v < npad; v += THREADS) {
         g0[v] = make_uint2(0u, 0u);
         g1[v] = make_uint2(0u, 0u);
+        gf0[v] = R(0);
+        gf1[v] = R(0);
     }
     if (tid == 0) sh.ctr = 0;
     __syncthreads();
@@ -205,7 +221,10 @@ __global__ void __launch_bounds__(THREADS, 1) fused_cluster_kernel(const DevView
     for (int it = 0; it < A.sp.T; ++it) {
         U *const gw = (it & 1) ? g1 : g0;
         U *const gz = (it & 1) ? g0 : g1;
+        R *const gfw = (it & 1) ? gf1 : gf0;
+        R *const gfz = (it & 1) ? gf0 : gf1;
         G.g = gw;
+        G.gf = gfw;
         eval_tasks_strided<R, NR, NI, SMEM_FULL>(V, S, xs, G, sh.ctr, rank, CL, it);
         cluster_barrier();  // also ends the evaluation of this CTA's warps
         for (int v = tid; v < n; v += THREADS) {
@@ -217,8 +236,15 @@ __global__ void __launch_bounds__(THREADS, 1) fused_cluster_kernel(const DevView
                 hs += (int)p.y;
             }
             const long long gi = (long long)((unsigned long long)hs << fl) + (long long)ls;
+            R z = fma(-lrs, R(gi), xs[v]);
+            if (prods) {  // the same for every thread
+                R gp = ld_peer(gfw, v, 0);
+                for (int q = 1; q < CL; ++q) gp += ld_peer(gfw, v, q);
+                z = fma(-R(A.sp.lr), gp, z);
+                gfz[v] = R(0);
+            }
             // clip to [-1, 1] on the integer pipes: |z| > 1 becomes sign(z) 1
-            long long zb = __double_as_longlong(fma(-lrs, R(gi), xs[v]));
+            long long zb = __double_as_longlong(z);
             if ((zb & 0x7fffffffffffffffll) > 0x3ff0000000000000ll) zb = (zb & (long long)0x8000000000000000ull) | 0x3ff0000000000000ll;
             xs[v] = __longlong_as_double(zb);
             gz[v] = make_uint2(0u, 0u);

@@ -520,14 +520,16 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
 int smem_mode_for(int n, size_t elem, size_t image_bytes, int max_smem, size_t &bytes) {
     const size_t npad = ((size_t)n + 2 + 3) & ~size_t(3);  // two dummy variables, rounded to 4
     const size_t budget = max_smem > 2048 ? (size_t)max_smem - 1024 : 0;
-    // FP32 resident mode keeps the gradient as two int32 words and one FP32 word per variable
-    const size_t res_xg = elem == 4 ? 4 * npad * 4 : 2 * npad * elem;
+    // FP32 resident mode keeps the gradient as two int32 words and one FP32 word per
+    // variable; FP64 keeps two int32 fixed-point words and one FP64 product word
+    const size_t xg = elem == 4 ? 2 * npad * 4 : 3 * npad * 8;
+    const size_t res_xg = elem == 4 ? 4 * npad * 4 : xg;
     if (res_xg + image_bytes <= budget) {
         bytes = res_xg + image_bytes;
         return SMEM_RES;
     }
-    if (2 * npad * elem <= budget) {
-        bytes = 2 * npad * elem;
+    if (xg <= budget) {
+        bytes = xg;
         return SMEM_FULL;
     }
     if (npad * elem <= budget) {
@@ -1458,6 +1460,7 @@ int ffsat_load_instance(int32_t n_vars, int32_t n_cons, const int64_t *row_ptr, 
     V.fix64_s = P->fix64_s;
     V.fix64_i = P->fix64_i;
     V.fix64_l = P->fix64_l;
+    V.has_prod = (int32_t)seg_len.size() > P->n_node_seg ? 1 : 0;
     V.row_ptr = reinterpret_cast<const int32_t *>(base + o_rp);
     V.lits = reinterpret_cast<const int32_t *>(base + o_lits);
     V.type = reinterpret_cast<const uint8_t *>(base + o_type);
@@ -1573,12 +1576,19 @@ static ClusterFn cluster_launcher(int nr) {
 // CTAs per point for an FP64 fixed-step call on B points (ffsat_options.cluster):
 // 1 for the one-CTA kernel, else the cluster size, with the cluster kernel's
 // dynamic shared memory and the offset of its second gradient buffer.
-static int step_cluster_size(ffsat_instance *I, int32_t B, int mode, size_t &smem, size_t &g1_off) {
+static int step_cluster_size(ffsat_instance *I, int32_t B, int mode, size_t &smem, size_t &g1_off, int &cmode) {
     const int opt = I->opt.cluster;
     if (opt == 1 || (mode != SMEM_FULL && mode != SMEM_RES) || !I->fix64_ok) return 1;
     const size_t npad = ((size_t)I->n + 2 + 3) & ~size_t(3);
-    g1_off = (I->smem64 + 15) & ~size_t(15);
-    smem = g1_off + npad * sizeof(double);
+    // the one-CTA layout, then the second fixed-point and FP64 product words; a
+    // resident image that leaves no room for them stays in global memory
+    auto layout = [&](int m) {
+        g1_off = ((m == SMEM_RES ? I->smem64 : 3 * npad * sizeof(double)) + 15) & ~size_t(15);
+        smem = g1_off + 2 * npad * sizeof(double);
+    };
+    cmode = mode;
+    layout(cmode);
+    if (smem + 1024 > (size_t)I->max_smem && cmode == SMEM_RES) layout(cmode = SMEM_FULL);
     if (smem + 1024 > (size_t)I->max_smem) return 1;
     // more than half of an SM's shared memory: one CTA per SM, so that the CTAs of
     // the clusters do not share an SM's FP64 pipe while other SMs idle
@@ -1591,7 +1601,7 @@ static int step_cluster_size(ffsat_instance *I, int32_t B, int mode, size_t &sme
         std::lock_guard<std::mutex> lock(I->cluster_mu);
         if (I->cluster_active[k] < 0) {
             int active = 0;
-            if (cluster_launcher(I->nr64)(I->V64, mode, FusedArgs{}, smem, g1_off, 1, cl, nullptr, &active) !=
+            if (cluster_launcher(I->nr64)(I->V64, cmode, FusedArgs{}, smem, g1_off, 1, cl, nullptr, &active) !=
                 cudaSuccess) {
                 (void)cudaGetLastError();
                 active = 0;
@@ -1623,10 +1633,11 @@ static bool step_pairs(const ffsat_instance *I, bool f64, int mode, const FusedA
 static int launch_step(ffsat_instance *I, bool f64, int mode, const FusedArgs &a, int32_t B, void *stream) {
     const DevView &V = f64 ? I->V64 : I->V32;
     size_t csmem = 0, g1_off = 0;
-    const int cl = f64 ? step_cluster_size(I, B, mode, csmem, g1_off) : 1;
+    int cmode = mode;
+    const int cl = f64 ? step_cluster_size(I, B, mode, csmem, g1_off, cmode) : 1;
     bool pairs = false;
     if (cl > 1) {
-        CUDA_TRY(cluster_launcher(I->nr64)(V, mode, a, csmem, g1_off, B, cl, static_cast<cudaStream_t>(stream),
+        CUDA_TRY(cluster_launcher(I->nr64)(V, cmode, a, csmem, g1_off, B, cl, static_cast<cudaStream_t>(stream),
                                            nullptr));
     } else if ((pairs = step_pairs(I, f64, mode, a, B))) {
         // two points per CTA: the second point's x and gradient words after the image

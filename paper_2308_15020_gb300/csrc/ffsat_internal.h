@@ -108,7 +108,8 @@ struct DevView {
     // variable: g = (hi 2^L + lo) / 2^S64; fix64_s = 2^S64, fix64_i = 2^-S64,
     // fix64_l = L
     double fix64_s, fix64_i;
-    int32_t fix64_l, pad3;
+    int32_t fix64_l;
+    int32_t has_prod;  // the image has product-path segments (FP64: FP64 product words in use)
     // start value of both fixed-point words of variable v (npad entries):
     // -(fixed-point contributions v receives per evaluation) * 0x4B400000 mod 2^32
     const int32_t *fix_bias;

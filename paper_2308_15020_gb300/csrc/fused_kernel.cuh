@@ -225,7 +225,8 @@ struct PlainAcc {
 struct Fix64Acc {
     static constexpr bool kDummySlots = true;  // npad >= n + 2 words
     static constexpr double kRound = 6755399441055744.0;  // 1.5 * 2^52
-    uint2 *g;  // {lo, hi} per variable
+    uint2 *g;    // {lo, hi} per variable
+    double *gf;  // product contributions (FP64 atomics; see addf)
     double s, inv;  // 2^S64 and 2^-S64
     int l;
     // m = fma(a, b, kRound): adds round(a b) to variable v
@@ -238,14 +239,21 @@ struct Fix64Acc {
         asm volatile("red.shared.add.s32 [%0+4], %1;" ::"r"(a), "r"(hi) : "memory");
     }
     __device__ __forceinline__ void add(uint32_t v, double c) const { put(v, fma(c, s, kRound)); }
-    __device__ __forceinline__ void addf(uint32_t v, double c) const { add(v, c); }
-    // g = (hi 2^L + lo) 2^-S64
-    __device__ __forceinline__ double get(int v) const {
-        const uint2 w = g[v];
+    // Product contributions (XORs and long clauses: products of many factors)
+    // can lie far below the fixed point's resolution, as in the FP32
+    // accumulator: they go to an FP64 word with atomicAdd, keeping their
+    // relative precision (and the order of these additions is not fixed).
+    __device__ __forceinline__ void addf(uint32_t v, double c) const { atomicAdd(&gf[v], c); }
+    // g = (hi 2^L + lo) 2^-S64 + gf
+    __device__ __forceinline__ double fixed(uint2 w) const {
         const long long G = (long long)((unsigned long long)(long long)(int)w.y << l) + (long long)w.x;
         return (double)G * inv;
     }
-    __device__ __forceinline__ void zero(int v) const { g[v] = make_uint2(0u, 0u); }
+    __device__ __forceinline__ double get(int v) const { return fixed(g[v]) + gf[v]; }
+    __device__ __forceinline__ void zero(int v) const {
+        g[v] = make_uint2(0u, 0u);
+        gf[v] = 0.0;
+    }
 };
 
 // Clause and node contributions (bounded by their weight) go to the fixed-point
@@ -860,7 +868,8 @@ template <typename R, int SM>
 __device__ __forceinline__ size_t image_offset(int n) {
     const int npad = (n + 2 + 3) & ~3;
     constexpr bool FIX = SM == SMEM_RES && sizeof(R) == 4;
-    return FIX ? 4 * (size_t)npad * 4 : 2 * (size_t)npad * sizeof(R);
+    // FP32 resident: x | hi | lo | gf; FP64: x | fixed-point words | FP64 product word
+    return FIX ? 4 * (size_t)npad * 4 : (sizeof(R) == 8 ? 3 : 2) * (size_t)npad * sizeof(R);
 }
 
 // Constraint-data view for the point loop; SMEM_RES copies the image into shared
@@ -1039,6 +1048,7 @@ __device__ __forceinline__ void run_point(const DevView &V, const FusedArgs &A, 
         glen = npad;
     } else if constexpr (FIX64) {
         G.g = reinterpret_cast<uint2 *>(gs);
+        G.gf = gs + npad;
         G.s = V.fix64_s;
         G.inv = V.fix64_i;
         G.l = V.fix64_l;

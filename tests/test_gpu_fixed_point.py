@@ -151,9 +151,10 @@ def test_two_points_per_cta_through_noalloc_and_graph():
     ("hub_degree_5000", _hub, 1),  # the fixed point would resolve only 2^-36: gradient in a global row
 ])
 def test_fp64_fixed_point_eval_and_step(name, make, mode):
-    """FP64 with the gradient in shared memory accumulates it in two-word fixed
-    point: within 1e-10 of the oracle, and repeated calls give the same bits; an
-    instance whose range would make it coarser keeps FP64 atomics in global rows."""
+    """FP64 with the gradient in shared memory accumulates clause and node
+    contributions in two-word fixed point: within 1e-10 of the oracle, and
+    without product constraints repeated calls give the same bits; an instance
+    whose range would make it coarser keeps FP64 atomics in global rows."""
     from paper_2308_15020_gb300 import ffsat
 
     inst = make()
@@ -166,7 +167,7 @@ def test_fp64_fixed_point_eval_and_step(name, make, mode):
         outs.append((to_np(f), to_np(g)))
     ef, eg = compare(inst, x, outs[0][0], outs[0][1], 1e-10)
     assert ef <= 1 and eg <= 1, (ef, eg)
-    if mode == 3:
+    if mode == 3 and name == "3sat_n100":
         assert np.array_equal(outs[0][1].view(np.uint64), outs[1][1].view(np.uint64))
     xa = torch.from_numpy(x.copy()).cuda()
     xb = torch.from_numpy(x.copy()).cuda()
@@ -174,5 +175,25 @@ def test_fp64_fixed_point_eval_and_step(name, make, mode):
     h.step(xb, T=20, lr=0.05, seed=1, epoch=1, restart=False)
     xo, _, _ = O.step(inst, x, T=20, lr=0.05, seed=1, epoch=1, restart=False)
     assert np.max(np.abs(to_np(xa) - xo)) < 1e-9
-    if mode == 3:
+    if mode == 3 and name == "3sat_n100":
         assert torch.equal(xa, xb)
+
+
+@pytest.mark.parametrize("cluster", [1, 0])
+def test_fp64_xor_only_relative_precision(cluster):
+    """An XOR-only instance (parity learning, XORs of about N/2 literals): the
+    gradient of a variable is a sum of products of many factors and can be tiny,
+    and the FP64 paths keep it to 1e-10 of its own condition scale (product
+    contributions are not rounded to the fixed point's absolute resolution)."""
+    from paper_2308_15020_gb300 import ffsat
+
+    inst = gen.parity_learning(40, 3)
+    h = ffsat.Instance(inst, cluster=cluster)
+    x = gen.uniform_points(8, inst.n, 4, dtype=np.float64)
+    f, g = h.eval_grad(torch.from_numpy(x).cuda())
+    ef, eg = compare(inst, x, to_np(f), to_np(g), 1e-10)
+    assert ef <= 1 and eg <= 1, (ef, eg)
+    xs = torch.from_numpy(x.copy()).cuda()
+    h.step(xs, T=10, lr=0.5, seed=1, epoch=1, restart=False)
+    xo, _, _ = O.step(inst, x, T=10, lr=0.5, seed=1, epoch=1, restart=False)
+    assert np.max(np.abs(to_np(xs) - xo)) < 1e-10
