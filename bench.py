@@ -410,7 +410,7 @@ def alu_peak_source(alu, name: str) -> str:
 
 
 def sec8d_hbm_bytes(st, B: int, T: int, elem: int) -> float:
-    """HBM bytes of T evaluations by the survey's per-evaluation model: read x
+    """HBM bytes of T evaluations by the per-evaluation traffic model: read x
     and write g (2 B n elem) plus f (8 B)."""
     return T * (2.0 * B * st["n"] * elem + 8.0 * B)
 
@@ -1126,7 +1126,7 @@ def run_ours(args, rank: int, world: int, local_rank: int):
                 "smem": {"achieved": smem_bytes / launch_s / 1e9,
                          "peak": n_sm * SMEM_BYTES_PER_CLK_SM * sm_max * 1e6 / 1e9, "unit": "GB/s"}}
     elif not alu_bound and resident:
-        # the survey's model of this workload: memory/gather-bound, 2 B n 4 + 8 B
+        # the per-evaluation traffic model of this workload: memory/gather-bound, 2 B n 4 + 8 B
         # bytes per evaluation; x and the gradient stay in shared memory for all T
         # iterations here, so the on-chip shared-memory pipe is the bound that the
         # kernel actually meets (reported beside it)
