@@ -493,11 +493,12 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
             for (; c + 32 * kk <= end; c += 32 * kk) ts.tasks.push_back(make_int4(kind, c, 32 * kk, 0));
     }
     // node tasks first (the longest), then product tasks spread evenly among the
-    // first three quarters of the clause tasks: their long dependent chains
-    // overlap with clause work in other warps instead of all warps starting on
-    // them at once, and the end of every iteration is left to short clause tasks
-    // (CNF-XOR step: products first 2.43 ms, spread over all clause tasks 2.39 ms,
-    // over the first three quarters 2.24 ms; over a half 2.27 ms)
+    // first quarter of the clause tasks: their long dependent chains overlap
+    // with clause work in other warps instead of all warps starting on them at
+    // once, and the end of every iteration is left to short clause tasks
+    // (CNF-XOR step, two points per CTA: over the first three quarters 1.516 ms,
+    // a half 1.473, a quarter 1.474; one point per CTA, 152 points: 0.972 and,
+    // over a quarter, 0.950 ms)
     {
         std::vector<int4> node, prod, rest;
         for (const int4 &t : ts.tasks) {
@@ -506,7 +507,7 @@ void build_tasks(const std::vector<int32_t> &seg_len, int n_node_seg, int n_clau
         }
         std::vector<int4> out = node;
         const size_t np = prod.size(), nc = rest.size();
-        const size_t nc_mix = (nc * 3) / 4;
+        const size_t nc_mix = nc / 4;
         size_t ip = 0, ic = 0;
         while (ip < np || ic < nc) {
             // keep the product share of the emitted tasks at np / (np + nc_mix)
